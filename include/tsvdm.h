@@ -1,0 +1,201 @@
+/*
+ * tsvdm.h - C ABI of the GB300 (sm_103a) star-M truncated tensor SVD library.
+ *
+ * The operations follow arXiv 2605.16058 ("High-Performance star-M SVD for Big Data
+ * Compression"):
+ *   - mode-3 TTM  Ahat = A x_3 M                         (Sec. 2.1, Sec. 3.1)
+ *   - t-SVDM-I: per-slice truncated SVD at uniform rank k (Sec. 3.3, Fig. 1)
+ *   - t-SVDM-II: global sigma^2 threshold from a relative error tolerance, per-slice
+ *     ranks rho_i and a variable-rank packed format       (Algorithm 2, Sec. 3.4)
+ *   - reconstruction  X_k = (U S V^T per slice) x_3 M^{-1} (Sec. 2.1, Sec. 2.2)
+ *   - the gradient of the truncation error with respect to X and M (an extension: the
+ *     paper has no differentiation; see tsvdm_backward).
+ *
+ * Conventions shared by every entry point
+ *   Layout   column-major throughout.  An n1 x n2 x n3 tensor X has X(a,b,t) at
+ *            X[a + n1*b + n1*n2*t]; frontal slice t is contiguous (Sec. 3).  An n x n
+ *            matrix M has M(i,t) at M[i + n*t]; row i of M forms output slice i.
+ *   Types    dtype TSVDM_F32 means every tensor/matrix argument is float, TSVDM_F64
+ *            means double.  Sizes are int64_t.
+ *   Memory   tensor arguments are caller-owned.  Unless an entry point says otherwise
+ *            they must be DEVICE pointers.  tsvdm_fixed_rank and tsvdm_tolerance also
+ *            accept HOST pointers (pageable or pinned; detected per pointer): inputs
+ *            are copied in and outputs copied out on the plan's stream, through
+ *            staging buffers the plan allocates on the first such call and keeps.
+ *   Streams  work is enqueued on the plan's stream.  Calls return once the work is
+ *            enqueued, except where a host output (rel_err, total_rank, loss) is
+ *            requested: those calls synchronise the stream before returning.
+ *   Errors   argument errors are detected on the host and returned at once, with
+ *            nothing enqueued.  Errors found on the device (no convergence, non-finite
+ *            values, a bounded wait that ran out) are recorded in the plan's status
+ *            word; synchronous calls return them, and tsvdm_last_status() reads them
+ *            after the caller has synchronised the stream.  No device code traps.
+ *   Threads  a plan may be used by one host thread at a time.
+ */
+#ifndef TSVDM_H
+#define TSVDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TSVDM_OK = 0,
+  TSVDM_EINVAL = 1,      /* bad argument: sizes, null pointer, k outside [1, min(n1,n2)],
+                            eps outside (0,1), dtype/precision mismatch               */
+  TSVDM_ENOTORTHO = 2,   /* the operation needs an orthogonal M (t-SVDM-II, original-
+                            domain factors) and the plan was not created with one     */
+  TSVDM_ENOCONV = 3,     /* a slice's Jacobi iteration reached the sweep cap; outputs
+                            are written from the last iterate                        */
+  TSVDM_ENONFINITE = 4,  /* NaN or Inf met in the transformed slices                  */
+  TSVDM_ETIMEOUT = 5,    /* a bounded device-side wait ran out                        */
+  TSVDM_ENOMEM = 6,      /* device or pinned-host allocation failed                   */
+  TSVDM_ECAPACITY = 7,   /* t-SVDM-II: the output capacity is below the total rank    */
+  TSVDM_ECUDA = 8,       /* a CUDA runtime call failed                                */
+  TSVDM_ENOTSUP = 9      /* combination not supported (e.g. TF32 precision with F64)  */
+} tsvdm_status;
+
+typedef enum { TSVDM_F32 = 0, TSVDM_F64 = 1 } tsvdm_dtype;
+
+/* Arithmetic of the mode-3 TTMs.  The slice SVDs run in the storage precision (FP32
+ * data with FP64 rotation angles and convergence test for F32; FP64 for F64).
+ *   TSVDM_P_FP64    FP64 CUDA-core products (dtype F64 only)
+ *   TSVDM_P_FP32    FP32 CUDA-core products (dtype F32)
+ *   TSVDM_P_TF32    one TF32 tensor-core product, FP32 accumulation (dtype F32)
+ *   TSVDM_P_BF16X3  split x = hi + lo in BF16, hi*hi + hi*lo + lo*hi on tensor cores,
+ *                   FP32 accumulation (dtype F32)                                   */
+typedef enum {
+  TSVDM_P_FP64 = 0,
+  TSVDM_P_FP32 = 1,
+  TSVDM_P_TF32 = 2,
+  TSVDM_P_BF16X3 = 3
+} tsvdm_prec;
+
+typedef struct tsvdm_plan_s *tsvdm_plan;
+
+/* Create a plan for n1 x n2 x n3 tensors (Sec. 2.2 problem statement: A in
+ * R^{m x p x n}, invertible M in R^{n x n}).  The plan owns all device workspace
+ * (allocated here, about (n1 n2 + min(n1,n2)^2) n3 elements plus O(n1 n2 + n3^2)), the
+ * device status word and the tile choices.  m_is_orthogonal declares M to be a
+ * nonzero multiple of an orthogonal matrix (Sec. 2.1): then M^{-1} = M^T / c^2 with
+ * c^2 = ||M(:,0)||^2, and t-SVDM-II is allowed.  stream is a cudaStream_t (NULL = the
+ * default stream).  Returns EINVAL for non-positive sizes, ENOTSUP for a precision the
+ * dtype cannot use, ENOMEM if the workspace cannot be allocated. */
+tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype dtype,
+                               tsvdm_prec prec, int m_is_orthogonal, void *stream,
+                               tsvdm_plan *out);
+tsvdm_status tsvdm_plan_destroy(tsvdm_plan plan);
+
+/* Jacobi controls.  tol is the relative off-diagonal threshold
+ * |a_i^T a_j| <= tol ||a_i|| ||a_j|| under which a column pair counts as orthogonal
+ * (<= 0 restores the default: 4 sqrt(m) u with u the unit roundoff of the dtype);
+ * max_sweeps caps the sweeps per slice (<= 0 restores the default 40).  A slice that
+ * is still rotating after max_sweeps sets TSVDM_ENOCONV. */
+tsvdm_status tsvdm_plan_set_jacobi(tsvdm_plan plan, double tol, int max_sweeps);
+
+/* Y = X x_3 M (inverse = 0) or Y = X x_3 M^{-1} (inverse = 1), Sec. 2.1.  For
+ * inverse = 1 on an orthogonal plan, M is the forward matrix and M^T / c^2 is applied;
+ * on a non-orthogonal plan, M must already hold M^{-1}.  X, Y: n1 x n2 x n3 device,
+ * X and Y must not overlap.  M: n3 x n3 device. */
+tsvdm_status tsvdm_transform(tsvdm_plan plan, const void *X, const void *M, int inverse,
+                             void *Y);
+
+/* t-SVDM-I (Sec. 3.3; Fig. 1): Ahat = X x_3 M, then the leading k singular triplets of
+ * every frontal slice of Ahat.  Outputs, all caller-owned (device or host):
+ *   U  n1 x k x n3   U(:,j,i) = j-th left singular vector of Ahat(:,:,i)
+ *   S  k x n3        S(j,i) = j-th singular value of slice i, descending in j
+ *   V  n2 x k x n3   right singular vectors
+ * Signs: the largest-magnitude entry of each left vector is positive.
+ * original_domain = 0 returns the transform-domain factors Uhat, Shat, Vhat (the
+ * compressed form, Fig. 1); 1 returns them mapped back by M^{-1} along mode 3 (Sec.
+ * 2.2), which needs an orthogonal plan (else ENOTORTHO); S is then f-diagonal data
+ * S(j,:) = Shat(j,:) x M^{-T}, not sorted and possibly negative.
+ * rel_err (host, nullable): sqrt(sum of discarded sigma^2 / sum of all sigma^2), which
+ * equals ||X - X_k||_F / ||X||_F when M is a multiple of an orthogonal matrix
+ * (Eckart-Young, Sec. 2.3); NaN on a non-orthogonal plan.  Requesting it synchronises. */
+tsvdm_status tsvdm_fixed_rank(tsvdm_plan plan, const void *X, const void *M, int64_t k,
+                              void *U, void *S, void *V, int original_domain,
+                              double *rel_err);
+
+/* t-SVDM-II (Algorithm 2, "truncate" strategy of Sec. 3.4), orthogonal plans only
+ * (else ENOTORTHO).  eps in (0,1).  Steps: the full t-SVDM of X; v = all sigma^2
+ * sorted ascending; w = cumulative sums (FP64); J = the largest index with
+ * w_J / sum(v) < eps^2 (J = 0: nothing is discarded); tau = v_J;
+ * rho_i = #{sigma_{j,i}^2 > tau} (values equal to tau are discarded).
+ * Outputs (caller-owned; device or host):
+ *   ranks    int32 [n3]       rho_i
+ *   offsets  int64 [n3 + 1]   exclusive prefix sum of rho; offsets[n3] = total rank
+ *   U  n1 x capacity, S  capacity, V  n2 x capacity: slice i's triplets occupy columns
+ *            offsets[i] .. offsets[i+1]-1 (variable-rank format, no padding)
+ *   total_rank (host, required)   sum of rho_i
+ *   rel_err  (host, nullable)     sqrt(sum of discarded sigma^2 / sum of all sigma^2)
+ * U, S, V may all be NULL: only ranks, offsets and total_rank are produced and the
+ * factors stay in the plan for tsvdm_tolerance_pack.  If capacity < total rank the call
+ * returns ECAPACITY after writing ranks/offsets/total_rank; the factors also stay in
+ * the plan.  Always synchronises (the total rank is read back). */
+tsvdm_status tsvdm_tolerance(tsvdm_plan plan, const void *X, const void *M, double eps,
+                             int32_t *ranks, int64_t *offsets, void *U, void *S, void *V,
+                             int64_t capacity, int64_t *total_rank, double *rel_err);
+
+/* Packs the factors kept by the most recent tsvdm_tolerance call on this plan into
+ * device buffers U (n1 x capacity), S (capacity), V (n2 x capacity).  ECAPACITY if
+ * capacity is below that call's total rank; EINVAL if no tolerance call preceded. */
+tsvdm_status tsvdm_tolerance_pack(tsvdm_plan plan, void *U, void *S, void *V,
+                                  int64_t capacity);
+
+/* X_k = (U_i diag(S_i) V_i^T for every slice i) x_3 M^{-1}  (Sec. 2.1 third step).
+ * Factors are transform-domain, on the device.  offsets == NULL: uniform rank k,
+ * U n1 x k x n3, S k x n3, V n2 x k x n3.  offsets != NULL (device int64 [n3+1]):
+ * packed variable-rank factors as produced by tsvdm_tolerance (k is ignored).
+ * M: forward matrix on an orthogonal plan, else M^{-1}.  Xk: n1 x n2 x n3 device. */
+tsvdm_status tsvdm_reconstruct(tsvdm_plan plan, const void *U, const void *S, const void *V,
+                               const int64_t *offsets, int64_t k, const void *M, void *Xk);
+
+/* Gradient of the t-SVDM-I truncation loss (an extension; the paper has no
+ * differentiation):  L(X, M) = sqrt(E) / ||X||_F,  E = sum_i sum_{j>k} sigma_j(Ahat_i)^2,
+ * Ahat = X x_3 M.  With R_i = Ahat_i - U_i S_i V_i^T (the residual of the rank-k
+ * truncation, from the forward factors U, S, V of tsvdm_fixed_rank in the transform
+ * domain), dE/dAhat_i = 2 R_i where sigma_k > sigma_{k+1}, so
+ *   dX = dL * [ (R x_3 M^T) / (sqrt(E) ||X||) - L X / ||X||^2 ]     (n1 x n2 x n3)
+ *   dM = dL * R_(3)-view^T X_(3)-view / (sqrt(E) ||X||)             (n3 x n3)
+ * where the views are the (n1 n2) x n3 column-major matrices.  dL is the upstream
+ * scalar.  dX and dM are device, nullable.  E = 0 gives L = 0 and zero gradients.
+ * loss (host, nullable) receives L and synchronises. */
+tsvdm_status tsvdm_backward(tsvdm_plan plan, const void *X, const void *M, int64_t k,
+                            const void *U, const void *S, const void *V, double dL,
+                            void *dX, void *dM, double *loss);
+
+/* Device-detected status of the plan's work so far (ENOCONV, ENONFINITE, ETIMEOUT or
+ * OK).  Synchronises the plan's stream, then clears the word. */
+tsvdm_status tsvdm_last_status(tsvdm_plan plan);
+
+/* Number of Jacobi sweeps and rotations executed by the most recent decomposition on
+ * this plan (summed over slices); synchronises.  Either pointer may be NULL. */
+tsvdm_status tsvdm_plan_stats(tsvdm_plan plan, int64_t *sweeps, int64_t *rotations);
+
+const char *tsvdm_strerror(tsvdm_status s);
+
+/* ---- learned orthogonal transform (extension) -------------------------------------
+ * Cayley form M(A) = (I + W)^{-1} (I - W) M0 with W = A^T - A skew-symmetric.
+ * All pointers are n x n device matrices of the given dtype; stream is a cudaStream_t.
+ * tsvdm_cayley writes M and keeps Z = (I + W)^{-1} and Q = Z (I - W) in the caller's
+ * buffers for the backward.  (I + W) is always invertible for skew W and is solved by
+ * Gauss-Jordan elimination without pivoting (its symmetric part is I). */
+tsvdm_status tsvdm_cayley(int64_t n, tsvdm_dtype dtype, const void *A, const void *M0,
+                          void *M, void *Z, void *Q, void *stream);
+/* dA = (dW)^T - dW with dW = -Z^T (dM M0^T) (Q + I)^T. */
+tsvdm_status tsvdm_cayley_backward(int64_t n, tsvdm_dtype dtype, const void *M0,
+                                   const void *Z, const void *Q, const void *dM, void *dA,
+                                   void *work, void *stream);
+/* One Adam step (Kingma & Ba) over count elements, in place: step is 1-based. */
+tsvdm_status tsvdm_adam(int64_t count, tsvdm_dtype dtype, void *param, const void *grad,
+                        void *m1, void *m2, int64_t step, double lr, double beta1,
+                        double beta2, double eps, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSVDM_H */

@@ -17,6 +17,9 @@ Readings of the paper used here (where it is silent or ambiguous):
     and rho_i counts sigma^2 > tau strictly, so every value equal to tau is discarded;
   * J = 0 (no admissible index) discards nothing; an all-zero tensor keeps nothing and
     reports relative error 0;
+  * the reported relative error is sqrt(discarded sigma^2 / ||S||_F^2), Algorithm 2's
+    own normalisation, equal to the relative reconstruction error for any nonzero
+    multiple of an orthogonal M;
   * the truncation loss used for differentiation is the transform-domain relative error
     sqrt(sum of discarded sigma^2) / ||X||_F, equal to the original-domain error when M
     is orthogonal (Sec. 2.3);
@@ -154,8 +157,9 @@ def full_tsvdm(X, M, threads=None, max_sweeps=MAX_SWEEPS):
 def fixed_rank(X, M, k, threads=None, max_sweeps=MAX_SWEEPS):
     """t-SVDM-I: keep the leading k triplets of every transformed slice (hat domain).
 
-    rel_err is sqrt(sum of discarded sigma^2) / ||X||_F, the Eckart-Young value that
-    equals ||X - X_k||_F / ||X||_F when M is orthogonal (Sec. 2.3)."""
+    rel_err is sqrt(sum of discarded sigma^2 / sum of all sigma^2), the normalisation of
+    Algorithm 2 (||S||_F^2); by Eckart-Young (Sec. 2.3) it equals ||X - X_k||_F / ||X||_F
+    whenever M is a nonzero multiple of an orthogonal matrix."""
     X = _f64(X)
     full = full_tsvdm(X, M, threads=threads, max_sweeps=max_sweeps)
     r = full["S"].shape[0]
@@ -163,11 +167,11 @@ def fixed_rank(X, M, k, threads=None, max_sweeps=MAX_SWEEPS):
         raise ValueError("k must satisfy 1 <= k <= min(n1, n2)")
     S = full["S"]
     discarded = float(np.sum(S[k:, :] ** 2))
-    xn = frob(X)
+    total = float(np.sum(S ** 2))
     return dict(U=full["U"][:, :k, :].copy(order="F"), S=S[:k, :].copy(order="F"),
                 V=full["V"][:, :k, :].copy(order="F"), Ahat=full["Ahat"], S_all=S,
-                sweeps=full["sweeps"], discarded=discarded,
-                rel_err=(math.sqrt(discarded) / xn) if xn > 0 else 0.0)
+                sweeps=full["sweeps"], discarded=discarded, total=total,
+                rel_err=math.sqrt(discarded / total) if total > 0 else 0.0)
 
 
 # --------------------------------------------------------------------------------------
@@ -227,11 +231,11 @@ def tolerance(X, M, eps, threads=None, max_sweeps=MAX_SWEEPS):
         U[:, a:b] = full["U"][:, : b - a, i]
         S[a:b] = full["S"][: b - a, i]
         V[:, a:b] = full["V"][:, : b - a, i]
-    xn = frob(X)
+    tot2 = sel["total"]
     return dict(ranks=ranks, offsets=off, U=U, S=S, V=V, S_all=full["S"],
                 Ahat=full["Ahat"], sweeps=full["sweeps"], J=sel["J"], tau=sel["tau"],
-                total=sel["total"], discarded=sel["discarded"],
-                rel_err=(math.sqrt(sel["discarded"]) / xn) if xn > 0 else 0.0)
+                total=tot2, discarded=sel["discarded"],
+                rel_err=math.sqrt(sel["discarded"] / tot2) if tot2 > 0 else 0.0)
 
 
 # --------------------------------------------------------------------------------------

@@ -379,3 +379,12 @@ def test_adam_step_first_update_is_lr_times_sign():
     oracle.adam_step(p, g, m1, m2, 1, lr=1e-3)
     # first step: mhat = g, vhat = g^2, update = lr * g / (|g| + eps)
     assert np.allclose(p, [1.0 - 1e-3, -2.0 + 1e-3, 0.5], atol=1e-10)
+
+
+def test_rel_err_is_scale_free_for_multiples_of_orthogonal_m():
+    c = synth.smoke_case()
+    a = oracle.fixed_rank(c["X"], c["M"], 6)
+    b = oracle.fixed_rank(c["X"], 3.0 * c["M"], 6)
+    assert abs(a["rel_err"] - b["rel_err"]) < 1e-13
+    Xk = oracle.reconstruct(b["U"], b["S"], b["V"], c["M"].T / 3.0)
+    assert abs(oracle.rel_err_direct(c["X"], Xk) - b["rel_err"]) < 1e-12
