@@ -163,7 +163,8 @@ tsvdm_status tsvdm_reconstruct(tsvdm_plan plan, const void *U, const void *S, co
  *   dM = dL * R_(3)-view^T X_(3)-view / (sqrt(E) ||X||)             (n3 x n3)
  * where the views are the (n1 n2) x n3 column-major matrices.  dL is the upstream
  * scalar.  dX and dM are device, nullable.  E = 0 gives L = 0 and zero gradients.
- * loss (host, nullable) receives L and synchronises. */
+ * loss (nullable) receives L: a device pointer is written on the stream without
+ * synchronising, a host pointer after synchronising. */
 tsvdm_status tsvdm_backward(tsvdm_plan plan, const void *X, const void *M, int64_t k,
                             const void *U, const void *S, const void *V, double dL,
                             void *dX, void *dM, double *loss);
@@ -178,15 +179,35 @@ tsvdm_status tsvdm_plan_stats(tsvdm_plan plan, int64_t *sweeps, int64_t *rotatio
 
 const char *tsvdm_strerror(tsvdm_status s);
 
+/* Per-stage instrumentation (not in the paper, which reports stage timings only in
+ * prose, Sec. 3.4 and Sec. 4).  With enable != 0, later calls on the plan record CUDA
+ * events on the plan's stream around each stage.  tsvdm_plan_profile_read synchronises
+ * and returns, for the most recent call, the stage times in milliseconds
+ * (ms[TSVDM_STAGE_COUNT], 0 for stages that did not run) and the number of kernels the
+ * call launched (launches, nullable). */
+typedef enum {
+  TSVDM_STAGE_TTM = 0,        /* mode-3 TTMs (forward and back-transform)            */
+  TSVDM_STAGE_TRANSPOSE = 1,  /* slice transposition for n1 < n2                     */
+  TSVDM_STAGE_JACOBI = 2,     /* batched one-sided Jacobi sweeps                     */
+  TSVDM_STAGE_FINALIZE = 3,   /* column norms and per-slice descending order         */
+  TSVDM_STAGE_SELECT = 4,     /* t-SVDM-II sort, FP64 prefix sums, ranks, offsets    */
+  TSVDM_STAGE_EMIT = 5,       /* normalised, sign-fixed factor output / packing      */
+  TSVDM_STAGE_OTHER = 6,      /* reductions, products and small kernels              */
+  TSVDM_STAGE_COUNT = 7
+} tsvdm_stage;
+tsvdm_status tsvdm_plan_profile(tsvdm_plan plan, int enable);
+tsvdm_status tsvdm_plan_profile_read(tsvdm_plan plan, float *ms, int64_t *launches);
+
 /* ---- learned orthogonal transform (extension) -------------------------------------
  * Cayley form M(A) = (I + W)^{-1} (I - W) M0 with W = A^T - A skew-symmetric.
- * All pointers are n x n device matrices of the given dtype; stream is a cudaStream_t.
- * tsvdm_cayley writes M and keeps Z = (I + W)^{-1} and Q = Z (I - W) in the caller's
- * buffers for the backward.  (I + W) is always invertible for skew W and is solved by
- * Gauss-Jordan elimination without pivoting (its symmetric part is I). */
+ * All pointers are n x n device matrices of the given dtype unless stated otherwise;
+ * stream is a cudaStream_t.  tsvdm_cayley writes M and keeps Z = (I + W)^{-1} and
+ * Q = Z (I - W) in the caller's buffers for the backward; work holds 2 n^2 elements.
+ * (I + W) is always invertible for skew W and is solved by Gauss-Jordan elimination
+ * without pivoting (its symmetric part is I, so no pivot vanishes). */
 tsvdm_status tsvdm_cayley(int64_t n, tsvdm_dtype dtype, const void *A, const void *M0,
-                          void *M, void *Z, void *Q, void *stream);
-/* dA = (dW)^T - dW with dW = -Z^T (dM M0^T) (Q + I)^T. */
+                          void *M, void *Z, void *Q, void *work, void *stream);
+/* dA = (dW)^T - dW with dW = -Z^T (dM M0^T) (Q + I)^T; work holds 3 n^2 elements. */
 tsvdm_status tsvdm_cayley_backward(int64_t n, tsvdm_dtype dtype, const void *M0,
                                    const void *Z, const void *Q, const void *dM, void *dA,
                                    void *work, void *stream);

@@ -1,0 +1,629 @@
+// C ABI of libtsvdm (declared in include/tsvdm.h): plans, argument checks, host-buffer
+// staging and the order of the device kernels for each operation.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+using namespace tsvdm;
+
+namespace tsvdm {
+template <typename T>
+cudaError_t trunc_sums(const T *sig, int cols, int nslices, int64_t k, double *scal,
+                       cudaStream_t st);
+}
+
+enum { SC_INVSCALE = 9 };
+enum { STG_X = 0, STG_M, STG_U, STG_S, STG_V, STG_RANKS, STG_OFF, STG_COUNT };
+
+struct tsvdm_plan_s {
+  int64_t n1 = 0, n2 = 0, n3 = 0;
+  tsvdm_dtype dtype = TSVDM_F32;
+  tsvdm_prec prec = TSVDM_P_FP32;
+  int ortho = 0;
+  cudaStream_t st = nullptr;
+  int transposed = 0;
+  int64_t rows = 0, cols = 0;
+  size_t esz = 4;
+  void *Ahat = nullptr, *Wt = nullptr, *Vw = nullptr, *sig = nullptr, *keys = nullptr;
+  int *perm = nullptr, *sweeps = nullptr, *status = nullptr, *queue = nullptr;
+  int *ranks_ws = nullptr;
+  int64_t *off_ws = nullptr;
+  long long *rots = nullptr;
+  double *scal = nullptr;
+  double *splitk = nullptr;
+  size_t splitk_elems = 0;
+  double tol = 0.0;
+  int max_sweeps = 40;
+  int cluster_hint = 0, grid_hint = 0;
+  int tol_valid = 0;
+  int64_t tol_total = 0;
+  void *stage[STG_COUNT] = {};
+  size_t stage_bytes[STG_COUNT] = {};
+  // instrumentation
+  int profile = 0;
+  cudaEvent_t ev[2 * TSVDM_STAGE_COUNT] = {};
+  int ran[TSVDM_STAGE_COUNT] = {};
+  int64_t launches = 0;
+};
+
+namespace {
+
+tsvdm_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TSVDM_OK;
+  if (e == cudaErrorMemoryAllocation) return TSVDM_ENOMEM;
+  return TSVDM_ECUDA;
+}
+
+#define CK(expr)                                    \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return from_cuda(_e);    \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+double default_tol(const tsvdm_plan_s *p) {
+  double u = p->dtype == TSVDM_F32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
+  return 4.0 * sqrt((double)p->rows) * u;
+}
+
+void *work_matrix(tsvdm_plan_s *p) { return p->transposed ? p->Wt : p->Ahat; }
+
+// Start of a call: forget the previous call's stage record.
+void begin_call(tsvdm_plan_s *p) {
+  p->launches = 0;
+  for (int i = 0; i < TSVDM_STAGE_COUNT; ++i) p->ran[i] = 0;
+}
+// Brackets a stage with events when profiling (a stage may run more than once per call;
+// the bracket then spans from its first start to its last end).
+void stage_begin(tsvdm_plan_s *p, int s) {
+  if (p->profile && !p->ran[s]) cudaEventRecord(p->ev[2 * s], p->st);
+}
+void stage_end(tsvdm_plan_s *p, int s, int nlaunch) {
+  p->launches += nlaunch;
+  if (p->profile) cudaEventRecord(p->ev[2 * s + 1], p->st);
+  p->ran[s] = 1;
+}
+
+// Device buffer for a caller pointer: the pointer itself when it is device memory, else
+// a staging buffer of `bytes` (grown on demand) filled from host when `copy_in`.
+tsvdm_status stage_in(tsvdm_plan_s *p, int slot, const void *ptr, size_t bytes, bool copy_in,
+                      void **dev, bool *staged) {
+  *staged = false;
+  *dev = const_cast<void *>(ptr);
+  if (ptr == nullptr || is_device_ptr(ptr)) return TSVDM_OK;
+  if (p->stage_bytes[slot] < bytes) {
+    if (p->stage[slot]) cudaFree(p->stage[slot]);
+    p->stage[slot] = nullptr;
+    p->stage_bytes[slot] = 0;
+    CK(cudaMalloc(&p->stage[slot], bytes));
+    p->stage_bytes[slot] = bytes;
+  }
+  *dev = p->stage[slot];
+  *staged = true;
+  if (copy_in && bytes) CK(cudaMemcpyAsync(*dev, ptr, bytes, cudaMemcpyHostToDevice, p->st));
+  return TSVDM_OK;
+}
+
+tsvdm_status read_status(tsvdm_plan_s *p) {
+  int s = 0;
+  CK(cudaMemcpyAsync(&s, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  if (s) CK(cudaMemsetAsync(p->status, 0, sizeof(int), p->st));
+  if (s & ST_NONFINITE) return TSVDM_ENONFINITE;
+  if (s & ST_TIMEOUT) return TSVDM_ETIMEOUT;
+  if (s & ST_NOCONV) return TSVDM_ENOCONV;
+  return TSVDM_OK;
+}
+
+template <typename T>
+tsvdm_status run_ttm(tsvdm_plan_s *p, const T *X, int64_t P, const T *M, bool inverse, T *Y,
+                     double *sumsq) {
+  const int64_t n = p->n3;
+  stage_begin(p, TSVDM_STAGE_TTM);
+  int nl = 1;
+  if (!inverse) {
+    CK(ttm_simt<T>(X, P, n, M, n, n, false, Y, nullptr, nullptr, nullptr, sumsq, p->st));
+  } else if (p->ortho) {
+    CK(inv_scale<T>(M, n, p->scal + SC_INVSCALE, p->st));
+    CK(ttm_simt<T>(X, P, n, M, n, n, true, Y, p->scal + SC_INVSCALE, nullptr, nullptr, sumsq,
+                   p->st));
+    nl = 2;
+  } else {
+    CK(ttm_simt<T>(X, P, n, M, n, n, false, Y, nullptr, nullptr, nullptr, sumsq, p->st));
+  }
+  stage_end(p, TSVDM_STAGE_TTM, nl);
+  return TSVDM_OK;
+}
+
+// Algorithm 1: Ahat = X x_3 M, then the slice SVDs (sorted sigma and permutation kept).
+template <typename T>
+tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
+  p->tol_valid = 0;
+  const int64_t P = p->n1 * p->n2;
+  tsvdm_status s = run_ttm<T>(p, X, P, M, false, (T *)p->Ahat, nullptr);
+  if (s != TSVDM_OK) return s;
+  if (p->transposed) {
+    stage_begin(p, TSVDM_STAGE_TRANSPOSE);
+    CK(transpose_slices<T>((const T *)p->Ahat, p->n1, p->n2, p->n3, (T *)p->Wt, p->st));
+    stage_end(p, TSVDM_STAGE_TRANSPOSE, 1);
+  }
+  CK(cudaMemsetAsync(p->queue, 0, sizeof(int), p->st));
+  CK(cudaMemsetAsync(p->rots, 0, sizeof(long long) * p->n3, p->st));
+  JacobiParams jp;
+  jp.A = work_matrix(p);
+  jp.V = p->Vw;
+  jp.sA = p->rows * p->cols;
+  jp.sV = p->cols * p->cols;
+  jp.rows = (int)p->rows;
+  jp.cols = (int)p->cols;
+  jp.nslices = (int)p->n3;
+  jp.tol = p->tol > 0 ? p->tol : default_tol(p);
+  jp.max_sweeps = p->max_sweeps;
+  jp.queue = p->queue;
+  jp.status = p->status;
+  jp.sweeps = p->sweeps;
+  jp.rots = p->rots;
+  stage_begin(p, TSVDM_STAGE_JACOBI);
+  CK(jacobi_run<T>(jp, p->st, p->cluster_hint, p->grid_hint));
+  stage_end(p, TSVDM_STAGE_JACOBI, 1);
+  stage_begin(p, TSVDM_STAGE_FINALIZE);
+  CK(jacobi_finalize<T>((const T *)work_matrix(p), jp.sA, jp.rows, jp.cols, jp.nslices,
+                        (T *)p->sig, p->perm, p->st));
+  stage_end(p, TSVDM_STAGE_FINALIZE, 1);
+  return TSVDM_OK;
+}
+
+template <typename T>
+tsvdm_status emit(tsvdm_plan_s *p, int64_t k, const int *ranks, const int64_t *offsets, T *U,
+                  T *S, T *V) {
+  stage_begin(p, TSVDM_STAGE_EMIT);
+  CK(emit_factors<T>((const T *)work_matrix(p), p->rows * p->cols, (const T *)p->Vw,
+                     p->cols * p->cols, (int)p->rows, (int)p->cols, (int)p->n3,
+                     p->transposed != 0, (const T *)p->sig, p->perm, k, ranks, offsets, U, S, V,
+                     p->st));
+  stage_end(p, TSVDM_STAGE_EMIT, 1);
+  return TSVDM_OK;
+}
+
+template <typename T>
+tsvdm_status fixed_rank_impl(tsvdm_plan_s *p, const void *X, const void *M, int64_t k, void *U,
+                             void *S, void *V, int original_domain, double *rel_err) {
+  const size_t e = p->esz;
+  const int64_t n1 = p->n1, n2 = p->n2, n3 = p->n3;
+  void *dX, *dM, *dU, *dS, *dV;
+  bool sX, sM, sU, sS, sV;
+  tsvdm_status s;
+  if ((s = stage_in(p, STG_X, X, e * n1 * n2 * n3, true, &dX, &sX)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_M, M, e * n3 * n3, true, &dM, &sM)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_U, U, e * n1 * k * n3, false, &dU, &sU)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_S, S, e * k * n3, false, &dS, &sS)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_V, V, e * n2 * k * n3, false, &dV, &sV)) != TSVDM_OK) return s;
+  if ((s = decompose<T>(p, (const T *)dX, (const T *)dM)) != TSVDM_OK) return s;
+  if ((s = emit<T>(p, k, nullptr, nullptr, (T *)dU, (T *)dS, (T *)dV)) != TSVDM_OK) return s;
+  if (rel_err) {
+    stage_begin(p, TSVDM_STAGE_OTHER);
+    CK(trunc_sums<T>((const T *)p->sig, (int)p->cols, (int)n3, k, p->scal, p->st));
+    stage_end(p, TSVDM_STAGE_OTHER, 1);
+  }
+  if (original_domain) {
+    T *tmp = (T *)p->Ahat;   // free once the factors are emitted
+    struct { void *buf; int64_t P; } f[3] = {{dU, n1 * k}, {dS, k}, {dV, n2 * k}};
+    for (auto &x : f) {
+      if ((s = run_ttm<T>(p, (const T *)x.buf, x.P, (const T *)dM, true, tmp, nullptr)) != TSVDM_OK)
+        return s;
+      CK(cudaMemcpyAsync(x.buf, tmp, e * x.P * n3, cudaMemcpyDeviceToDevice, p->st));
+    }
+  }
+  if (sU) CK(cudaMemcpyAsync(U, dU, e * n1 * k * n3, cudaMemcpyDeviceToHost, p->st));
+  if (sS) CK(cudaMemcpyAsync(S, dS, e * k * n3, cudaMemcpyDeviceToHost, p->st));
+  if (sV) CK(cudaMemcpyAsync(V, dV, e * n2 * k * n3, cudaMemcpyDeviceToHost, p->st));
+  if (rel_err || sU || sS || sV) {
+    double sc[SC_COUNT];
+    CK(cudaMemcpyAsync(sc, p->scal, sizeof(sc), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    if (rel_err) {
+      if (!p->ortho) *rel_err = NAN;
+      else *rel_err = sc[SC_TOTAL] > 0 ? sqrt(sc[SC_DISCARD] / sc[SC_TOTAL]) : 0.0;
+    }
+    return read_status(p);
+  }
+  return TSVDM_OK;
+}
+
+template <typename T>
+tsvdm_status tolerance_impl(tsvdm_plan_s *p, const void *X, const void *M, double eps,
+                            int32_t *ranks, int64_t *offsets, void *U, void *S, void *V,
+                            int64_t capacity, int64_t *total_rank, double *rel_err) {
+  const size_t e = p->esz;
+  const int64_t n1 = p->n1, n2 = p->n2, n3 = p->n3;
+  void *dX, *dM;
+  bool sX, sM;
+  tsvdm_status s;
+  if ((s = stage_in(p, STG_X, X, e * n1 * n2 * n3, true, &dX, &sX)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_M, M, e * n3 * n3, true, &dM, &sM)) != TSVDM_OK) return s;
+  if ((s = decompose<T>(p, (const T *)dX, (const T *)dM)) != TSVDM_OK) return s;
+  stage_begin(p, TSVDM_STAGE_SELECT);
+  CK(select_ranks<T>((const T *)p->sig, (int)p->cols, (int)n3, eps, p->keys, p->scal,
+                     p->ranks_ws, p->off_ws, p->st));
+  stage_end(p, TSVDM_STAGE_SELECT, 1);
+  double sc[SC_COUNT];
+  CK(cudaMemcpyAsync(sc, p->scal, sizeof(sc), cudaMemcpyDeviceToHost, p->st));
+  if (ranks)
+    CK(cudaMemcpyAsync(ranks, p->ranks_ws, sizeof(int32_t) * n3, cudaMemcpyDefault, p->st));
+  if (offsets)
+    CK(cudaMemcpyAsync(offsets, p->off_ws, sizeof(int64_t) * (n3 + 1), cudaMemcpyDefault, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  const int64_t tot = (int64_t)sc[SC_TOTRANK];
+  *total_rank = tot;
+  if (rel_err) *rel_err = sc[SC_TOTAL] > 0 ? sqrt(sc[SC_DISCARD] / sc[SC_TOTAL]) : 0.0;
+  p->tol_valid = 1;
+  p->tol_total = tot;
+  tsvdm_status dev = read_status(p);
+  if (!U && !S && !V) return dev;
+  if (capacity < tot) return TSVDM_ECAPACITY;
+  if ((s = tsvdm_tolerance_pack(p, U, S, V, capacity)) != TSVDM_OK) return s;
+  return dev;
+}
+
+template <typename T>
+tsvdm_status pack_impl(tsvdm_plan_s *p, void *U, void *S, void *V) {
+  const size_t e = p->esz;
+  const int64_t tot = p->tol_total;
+  void *dU, *dS, *dV;
+  bool sU, sS, sV;
+  tsvdm_status s;
+  if ((s = stage_in(p, STG_U, U, e * p->n1 * (tot > 0 ? tot : 1), false, &dU, &sU)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_S, S, e * (tot > 0 ? tot : 1), false, &dS, &sS)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_V, V, e * p->n2 * (tot > 0 ? tot : 1), false, &dV, &sV)) != TSVDM_OK) return s;
+  if (tot > 0) {
+    if ((s = emit<T>(p, 0, p->ranks_ws, p->off_ws, (T *)dU, (T *)dS, (T *)dV)) != TSVDM_OK) return s;
+    if (sU) CK(cudaMemcpyAsync(U, dU, e * p->n1 * tot, cudaMemcpyDeviceToHost, p->st));
+    if (sS) CK(cudaMemcpyAsync(S, dS, e * tot, cudaMemcpyDeviceToHost, p->st));
+    if (sV) CK(cudaMemcpyAsync(V, dV, e * p->n2 * tot, cudaMemcpyDeviceToHost, p->st));
+  }
+  if (sU || sS || sV) CK(cudaStreamSynchronize(p->st));
+  return TSVDM_OK;
+}
+
+template <typename T>
+tsvdm_status reconstruct_impl(tsvdm_plan_s *p, const void *U, const void *S, const void *V,
+                              const int64_t *offsets, int64_t k, const void *M, void *Xk) {
+  p->tol_valid = 0;
+  stage_begin(p, TSVDM_STAGE_OTHER);
+  CK(slice_products<T>((const T *)U, (const T *)S, (const T *)V, offsets, k, p->n1, p->n2, p->n3,
+                       (T *)p->Ahat, false, nullptr, p->st));
+  stage_end(p, TSVDM_STAGE_OTHER, 1);
+  return run_ttm<T>(p, (const T *)p->Ahat, p->n1 * p->n2, (const T *)M, true, (T *)Xk, nullptr);
+}
+
+template <typename T>
+tsvdm_status backward_impl(tsvdm_plan_s *p, const void *X, const void *M, int64_t k,
+                           const void *U, const void *S, const void *V, double dL, void *dX,
+                           void *dM, double *loss) {
+  p->tol_valid = 0;
+  const int64_t P = p->n1 * p->n2, n = p->n3;
+  CK(cudaMemsetAsync(p->scal, 0, sizeof(double) * SC_COUNT, p->st));
+  tsvdm_status s = run_ttm<T>(p, (const T *)X, P, (const T *)M, false, (T *)p->Ahat,
+                              p->scal + SC_XNORM2);
+  if (s != TSVDM_OK) return s;
+  stage_begin(p, TSVDM_STAGE_OTHER);
+  CK(slice_products<T>((const T *)U, (const T *)S, (const T *)V, nullptr, k, p->n1, p->n2, n,
+                       (T *)p->Ahat, true, p->scal + SC_E, p->st));
+  CK(backward_scalars(p->scal, dL, p->st));
+  stage_end(p, TSVDM_STAGE_OTHER, 2);
+  if (dX) {
+    stage_begin(p, TSVDM_STAGE_TTM);
+    CK(ttm_simt<T>((const T *)p->Ahat, P, n, (const T *)M, n, n, true, (T *)dX,
+                   p->scal + SC_ALPHA, p->scal + SC_BETA, (const T *)X, nullptr, p->st));
+    stage_end(p, TSVDM_STAGE_TTM, 1);
+  }
+  if (dM) {
+    stage_begin(p, TSVDM_STAGE_OTHER);
+    CK(gemm_atb<T>((const T *)p->Ahat, (const T *)X, P, n, (T *)dM, p->scal + SC_ALPHA,
+                   p->splitk, p->splitk_elems, p->st));
+    stage_end(p, TSVDM_STAGE_OTHER, 2);
+  }
+  if (loss && is_device_ptr(loss)) {
+    CK(cudaMemcpyAsync(loss, p->scal + SC_LOSS, sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+  } else if (loss) {
+    double sc[SC_COUNT];
+    CK(cudaMemcpyAsync(sc, p->scal, sizeof(sc), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    *loss = sc[SC_LOSS];
+  }
+  return TSVDM_OK;
+}
+
+bool valid_plan(tsvdm_plan p) { return p != nullptr && p->Ahat != nullptr; }
+
+void free_plan(tsvdm_plan_s *p) {
+  void *bufs[] = {p->Ahat, p->Wt, p->Vw, p->sig, p->keys, p->perm, p->sweeps, p->status,
+                  p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  for (int i = 0; i < STG_COUNT; ++i)
+    if (p->stage[i]) cudaFree(p->stage[i]);
+  for (int i = 0; i < 2 * TSVDM_STAGE_COUNT; ++i)
+    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tsvdm_strerror(tsvdm_status s) {
+  switch (s) {
+    case TSVDM_OK: return "success";
+    case TSVDM_EINVAL: return "invalid argument";
+    case TSVDM_ENOTORTHO: return "operation needs an orthogonal transform M";
+    case TSVDM_ENOCONV: return "Jacobi iteration reached the sweep cap";
+    case TSVDM_ENONFINITE: return "non-finite value in the transformed slices";
+    case TSVDM_ETIMEOUT: return "a bounded device wait ran out";
+    case TSVDM_ENOMEM: return "out of memory";
+    case TSVDM_ECAPACITY: return "output capacity below the total rank";
+    case TSVDM_ECUDA: return "CUDA runtime error";
+    case TSVDM_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype dtype,
+                               tsvdm_prec prec, int m_is_orthogonal, void *stream,
+                               tsvdm_plan *out) {
+  if (!out) return TSVDM_EINVAL;
+  *out = nullptr;
+  if (n1 <= 0 || n2 <= 0 || n3 <= 0) return TSVDM_EINVAL;
+  if (n1 > (1 << 30) || n2 > (1 << 30) || n3 > (1 << 30)) return TSVDM_EINVAL;
+  if (dtype != TSVDM_F32 && dtype != TSVDM_F64) return TSVDM_EINVAL;
+  if (dtype == TSVDM_F64 && prec != TSVDM_P_FP64) return TSVDM_ENOTSUP;
+  if (dtype == TSVDM_F32 && prec != TSVDM_P_FP32) return TSVDM_ENOTSUP;
+  tsvdm_plan_s *p = new (std::nothrow) tsvdm_plan_s();
+  if (!p) return TSVDM_ENOMEM;
+  p->n1 = n1;
+  p->n2 = n2;
+  p->n3 = n3;
+  p->dtype = dtype;
+  p->prec = prec;
+  p->ortho = m_is_orthogonal ? 1 : 0;
+  p->st = (cudaStream_t)stream;
+  p->esz = dtype == TSVDM_F32 ? 4 : 8;
+  p->transposed = n1 < n2;
+  p->rows = n1 < n2 ? n2 : n1;
+  p->cols = n1 < n2 ? n1 : n2;
+  const size_t e = p->esz;
+  const size_t nx = (size_t)n1 * n2 * n3;
+  const size_t nv = (size_t)p->cols * p->cols * n3;
+  const size_t ns = (size_t)p->cols * n3;
+  p->splitk_elems = (size_t)n3 * n3;
+  {
+    size_t splits = (size_t)8 * 1024 * 1024 / ((size_t)n3 * n3);
+    if (splits < 1) splits = 1;
+    if (splits > 256) splits = 256;
+    p->splitk_elems *= splits;
+  }
+  cudaError_t err = cudaSuccess;
+#define AL(ptr, bytes) \
+  if (err == cudaSuccess) err = cudaMalloc((void **)&(ptr), (bytes) > 0 ? (bytes) : 16)
+  AL(p->Ahat, e * nx);
+  if (p->transposed) AL(p->Wt, e * nx);
+  AL(p->Vw, e * nv);
+  AL(p->sig, e * ns);
+  AL(p->perm, sizeof(int) * ns);
+  AL(p->keys, 2 * sizeof(unsigned long long) * ns);
+  AL(p->sweeps, sizeof(int) * n3);
+  AL(p->rots, sizeof(long long) * n3);
+  AL(p->status, sizeof(int));
+  AL(p->queue, sizeof(int));
+  AL(p->ranks_ws, sizeof(int) * n3);
+  AL(p->off_ws, sizeof(int64_t) * (n3 + 1));
+  AL(p->scal, sizeof(double) * SC_COUNT);
+  AL(p->splitk, sizeof(double) * p->splitk_elems);
+#undef AL
+  if (err == cudaSuccess) err = cudaMemset(p->status, 0, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(p->scal, 0, sizeof(double) * SC_COUNT);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(p);
+    return err == cudaErrorMemoryAllocation ? TSVDM_ENOMEM : TSVDM_ECUDA;
+  }
+  *out = p;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_destroy(tsvdm_plan plan) {
+  if (!plan) return TSVDM_EINVAL;
+  cudaStreamSynchronize(plan->st);
+  free_plan(plan);
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_set_jacobi(tsvdm_plan plan, double tol, int max_sweeps) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  plan->tol = tol > 0 ? tol : 0.0;
+  plan->max_sweeps = max_sweeps > 0 ? max_sweeps : 40;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_transform(tsvdm_plan plan, const void *X, const void *M, int inverse,
+                             void *Y) {
+  if (!valid_plan(plan) || !X || !M || !Y || X == Y) return TSVDM_EINVAL;
+  begin_call(plan);
+  plan->tol_valid = 0;
+  const int64_t P = plan->n1 * plan->n2;
+  if (plan->dtype == TSVDM_F32)
+    return run_ttm<float>(plan, (const float *)X, P, (const float *)M, inverse != 0, (float *)Y,
+                          nullptr);
+  return run_ttm<double>(plan, (const double *)X, P, (const double *)M, inverse != 0, (double *)Y,
+                         nullptr);
+}
+
+tsvdm_status tsvdm_fixed_rank(tsvdm_plan plan, const void *X, const void *M, int64_t k, void *U,
+                              void *S, void *V, int original_domain, double *rel_err) {
+  if (!valid_plan(plan) || !X || !M || !U || !S || !V) return TSVDM_EINVAL;
+  begin_call(plan);
+  if (k < 1 || k > plan->cols) return TSVDM_EINVAL;
+  if (original_domain && !plan->ortho) return TSVDM_ENOTORTHO;
+  if (plan->dtype == TSVDM_F32)
+    return fixed_rank_impl<float>(plan, X, M, k, U, S, V, original_domain, rel_err);
+  return fixed_rank_impl<double>(plan, X, M, k, U, S, V, original_domain, rel_err);
+}
+
+tsvdm_status tsvdm_tolerance(tsvdm_plan plan, const void *X, const void *M, double eps,
+                             int32_t *ranks, int64_t *offsets, void *U, void *S, void *V,
+                             int64_t capacity, int64_t *total_rank, double *rel_err) {
+  if (!valid_plan(plan) || !X || !M || !total_rank) return TSVDM_EINVAL;
+  begin_call(plan);
+  if (!(eps > 0.0 && eps < 1.0)) return TSVDM_EINVAL;
+  if ((U || S || V) && !(U && S && V)) return TSVDM_EINVAL;
+  if (capacity < 0) return TSVDM_EINVAL;
+  if (!plan->ortho) return TSVDM_ENOTORTHO;
+  if (plan->dtype == TSVDM_F32)
+    return tolerance_impl<float>(plan, X, M, eps, ranks, offsets, U, S, V, capacity, total_rank,
+                                 rel_err);
+  return tolerance_impl<double>(plan, X, M, eps, ranks, offsets, U, S, V, capacity, total_rank,
+                                rel_err);
+}
+
+tsvdm_status tsvdm_tolerance_pack(tsvdm_plan plan, void *U, void *S, void *V, int64_t capacity) {
+  if (!valid_plan(plan) || !U || !S || !V) return TSVDM_EINVAL;
+  if (!plan->tol_valid) return TSVDM_EINVAL;
+  if (capacity < plan->tol_total) return TSVDM_ECAPACITY;
+  if (plan->dtype == TSVDM_F32) return pack_impl<float>(plan, U, S, V);
+  return pack_impl<double>(plan, U, S, V);
+}
+
+tsvdm_status tsvdm_reconstruct(tsvdm_plan plan, const void *U, const void *S, const void *V,
+                               const int64_t *offsets, int64_t k, const void *M, void *Xk) {
+  if (!valid_plan(plan) || !U || !S || !V || !M || !Xk) return TSVDM_EINVAL;
+  begin_call(plan);
+  if (!offsets && (k < 1 || k > plan->cols)) return TSVDM_EINVAL;
+  if (plan->dtype == TSVDM_F32)
+    return reconstruct_impl<float>(plan, U, S, V, offsets, k, M, Xk);
+  return reconstruct_impl<double>(plan, U, S, V, offsets, k, M, Xk);
+}
+
+tsvdm_status tsvdm_backward(tsvdm_plan plan, const void *X, const void *M, int64_t k,
+                            const void *U, const void *S, const void *V, double dL, void *dX,
+                            void *dM, double *loss) {
+  if (!valid_plan(plan) || !X || !M || !U || !S || !V) return TSVDM_EINVAL;
+  begin_call(plan);
+  if (k < 1 || k > plan->cols) return TSVDM_EINVAL;
+  if (plan->dtype == TSVDM_F32)
+    return backward_impl<float>(plan, X, M, k, U, S, V, dL, dX, dM, loss);
+  return backward_impl<double>(plan, X, M, k, U, S, V, dL, dX, dM, loss);
+}
+
+tsvdm_status tsvdm_plan_profile(tsvdm_plan plan, int enable) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  if (enable && !plan->ev[0]) {
+    for (int i = 0; i < 2 * TSVDM_STAGE_COUNT; ++i) CK(cudaEventCreate(&plan->ev[i]));
+  }
+  plan->profile = enable ? 1 : 0;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_profile_read(tsvdm_plan plan, float *ms, int64_t *launches) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  if (launches) *launches = plan->launches;
+  if (!ms) return TSVDM_OK;
+  CK(cudaStreamSynchronize(plan->st));
+  for (int s = 0; s < TSVDM_STAGE_COUNT; ++s) {
+    ms[s] = 0.f;
+    if (plan->profile && plan->ran[s]) CK(cudaEventElapsedTime(&ms[s], plan->ev[2 * s], plan->ev[2 * s + 1]));
+  }
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_last_status(tsvdm_plan plan) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  return read_status(plan);
+}
+
+tsvdm_status tsvdm_plan_stats(tsvdm_plan plan, int64_t *sweeps, int64_t *rotations) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  const int64_t n = plan->n3;
+  int *sw = (int *)malloc(sizeof(int) * n);
+  long long *ro = (long long *)malloc(sizeof(long long) * n);
+  if (!sw || !ro) {
+    free(sw);
+    free(ro);
+    return TSVDM_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(sw, plan->sweeps, sizeof(int) * n, cudaMemcpyDeviceToHost, plan->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ro, plan->rots, sizeof(long long) * n, cudaMemcpyDeviceToHost, plan->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(plan->st);
+  if (e == cudaSuccess) {
+    int64_t a = 0, b = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      a += sw[i] > 0 ? sw[i] : 0;
+      b += ro[i];
+    }
+    if (sweeps) *sweeps = a;
+    if (rotations) *rotations = b;
+  }
+  free(sw);
+  free(ro);
+  return from_cuda(e);
+}
+
+tsvdm_status tsvdm_cayley(int64_t n, tsvdm_dtype dtype, const void *A, const void *M0, void *M,
+                          void *Z, void *Q, void *work, void *stream) {
+  if (n <= 0 || !A || !M0 || !M || !Z || !Q || !work) return TSVDM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == TSVDM_F32)
+    return from_cuda(small_cayley<float>(n, (const float *)A, (const float *)M0, (float *)M,
+                                         (float *)Z, (float *)Q, (float *)work, st));
+  if (dtype == TSVDM_F64)
+    return from_cuda(small_cayley<double>(n, (const double *)A, (const double *)M0, (double *)M,
+                                          (double *)Z, (double *)Q, (double *)work, st));
+  return TSVDM_EINVAL;
+}
+
+tsvdm_status tsvdm_cayley_backward(int64_t n, tsvdm_dtype dtype, const void *M0, const void *Z,
+                                   const void *Q, const void *dM, void *dA, void *work,
+                                   void *stream) {
+  if (n <= 0 || !M0 || !Z || !Q || !dM || !dA || !work) return TSVDM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == TSVDM_F32)
+    return from_cuda(small_cayley_backward<float>(n, (const float *)M0, (const float *)Z,
+                                                  (const float *)Q, (const float *)dM, (float *)dA,
+                                                  (float *)work, st));
+  if (dtype == TSVDM_F64)
+    return from_cuda(small_cayley_backward<double>(n, (const double *)M0, (const double *)Z,
+                                                   (const double *)Q, (const double *)dM,
+                                                   (double *)dA, (double *)work, st));
+  return TSVDM_EINVAL;
+}
+
+tsvdm_status tsvdm_adam(int64_t count, tsvdm_dtype dtype, void *param, const void *grad,
+                        void *m1, void *m2, int64_t step, double lr, double beta1, double beta2,
+                        double eps, void *stream) {
+  if (count <= 0 || !param || !grad || !m1 || !m2 || step < 1) return TSVDM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == TSVDM_F32)
+    return from_cuda(small_adam<float>(count, (float *)param, (const float *)grad, (float *)m1,
+                                       (float *)m2, step, lr, beta1, beta2, eps, st));
+  if (dtype == TSVDM_F64)
+    return from_cuda(small_adam<double>(count, (double *)param, (const double *)grad,
+                                        (double *)m1, (double *)m2, step, lr, beta1, beta2, eps,
+                                        st));
+  return TSVDM_EINVAL;
+}
+
+}  // extern "C"

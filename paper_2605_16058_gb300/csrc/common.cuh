@@ -1,0 +1,111 @@
+// Internal declarations shared by the CUDA translation units of libtsvdm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tsvdm.h"
+
+namespace tsvdm {
+
+// Device status word bits (OR-ed by kernels, read back by the host).
+enum : int {
+  ST_NOCONV = 1,
+  ST_NONFINITE = 2,
+  ST_TIMEOUT = 4,
+};
+
+// Device scalars kept in the plan (FP64).
+enum : int {
+  SC_XNORM2 = 0,    // ||X||_F^2
+  SC_TOTAL = 1,     // sum of all sigma^2
+  SC_DISCARD = 2,   // sum of discarded sigma^2
+  SC_TAU = 3,       // t-SVDM-II threshold (a sigma^2 value)
+  SC_E = 4,         // backward: ||R||_F^2
+  SC_ALPHA = 5,     // backward: scale of the adjoint TTM
+  SC_BETA = 6,      // backward: scale of X in dX
+  SC_LOSS = 7,      // backward: L
+  SC_TOTRANK = 8,   // t-SVDM-II: total rank (as double, exact below 2^53)
+  SC_COUNT = 16
+};
+
+// ---- launch helpers implemented in the .cu files (all asynchronous on `st`) ----
+
+// Mode-3 TTM as a (P x n) x (n x J) product.  B(t,i) = M[i + ldm*t] (forward, M is J x n)
+// or M[t + ldm*i] (transB, M^T applied).  `scale_ptr` (device double, nullable) multiplies
+// the product; `beta_ptr` (device double, nullable) adds beta * Z[row + P*i] (Z same shape
+// as Y).  `sumsq` (device double, nullable) accumulates sum over X of x^2.
+template <typename T>
+cudaError_t ttm_simt(const T *X, int64_t P, int64_t n, const T *M, int64_t ldm, int64_t J,
+                     bool transB, T *Y, const double *scale_ptr, const double *beta_ptr,
+                     const T *Z, double *sumsq, cudaStream_t st);
+
+// Transposed copy of each m x p slice (rows x cols) into p x m.
+template <typename T>
+cudaError_t transpose_slices(const T *A, int64_t m, int64_t p, int64_t nslices, T *B,
+                             cudaStream_t st);
+
+struct JacobiParams {
+  void *A;             // slice s work matrix at A + s*sA: rows x cols, column-major
+  void *V;             // slice s rotations at V + s*sV: cols x cols
+  int64_t sA, sV;
+  int rows, cols;      // rows >= cols
+  int nslices;
+  double tol;
+  int max_sweeps;
+  int *queue;          // slice counter, zeroed before the launch
+  int *status;         // status word
+  int *sweeps;         // [nslices] sweeps executed (-1 = cap reached)
+  long long *rots;     // [nslices] rotations applied
+};
+
+template <typename T>
+cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int cluster_hint, int grid_hint);
+
+// sigma (sorted descending) and the column permutation of each slice.
+template <typename T>
+cudaError_t jacobi_finalize(const T *A, int64_t sA, int rows, int cols, int nslices, T *sig,
+                            int *perm, cudaStream_t st);
+
+// Writes normalised, sign-fixed factors of slices (see emit in jacobi.cu).
+template <typename T>
+cudaError_t emit_factors(const T *A, int64_t sA, const T *Vw, int64_t sV, int rows, int cols,
+                         int nslices, bool transposed, const T *sig, const int *perm,
+                         int64_t k_uniform, const int *ranks, const int64_t *offsets, T *U,
+                         T *S, T *V, cudaStream_t st);
+
+// t-SVDM-II selection (Algorithm 2) on the sorted singular values sig (cols x nslices).
+template <typename T>
+cudaError_t select_ranks(const T *sig, int cols, int nslices, double eps, void *keys_ws,
+                         double *scal, int *ranks, int64_t *offsets, cudaStream_t st);
+
+// Per-slice product Out_i = [Base_i -] U_i diag(S_i) V_i^T.
+template <typename T>
+cudaError_t slice_products(const T *U, const T *S, const T *V, const int64_t *offsets,
+                           int64_t k, int64_t n1, int64_t n2, int64_t n3, T *Out,
+                           bool subtract_from_out, double *sumsq, cudaStream_t st);
+
+// C (n x n) = alpha * A^T B with A, B column-major P x n; split over P; alpha from device.
+template <typename T>
+cudaError_t gemm_atb(const T *A, const T *B, int64_t P, int64_t n, T *C, const double *alpha,
+                     double *ws, size_t ws_elems, cudaStream_t st);
+
+template <typename T>
+cudaError_t sumsq(const T *X, int64_t count, double *out, cudaStream_t st);
+
+cudaError_t backward_scalars(double *scal, double dL, cudaStream_t st);
+
+// Orthogonality defect and squared norm of M's first column (scale of M^{-1} = M^T/c^2).
+template <typename T>
+cudaError_t inv_scale(const T *M, int64_t n, double *out, cudaStream_t st);
+
+template <typename T>
+cudaError_t small_cayley(int64_t n, const T *A, const T *M0, T *M, T *Z, T *Q, T *work,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t small_cayley_backward(int64_t n, const T *M0, const T *Z, const T *Q, const T *dM,
+                                  T *dA, T *work, cudaStream_t st);
+template <typename T>
+cudaError_t small_adam(int64_t count, T *param, const T *grad, T *m1, T *m2, int64_t step,
+                       double lr, double b1, double b2, double eps, cudaStream_t st);
+
+}  // namespace tsvdm

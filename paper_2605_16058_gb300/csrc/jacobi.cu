@@ -1,0 +1,634 @@
+// Batched one-sided Jacobi SVD of the frontal slices (the per-slice svd of Algorithm 1,
+// Sec. 3.2), laid out for GB300.
+//
+// Method: block one-sided (Hestenes) Jacobi.  A slice W (rows x cols, rows >= cols,
+// column-major, in place) is cut into column blocks of width B = W2/2.  One sweep runs
+// the round-robin tournament over the blocks (nb-1 rounds of nb/2 disjoint block
+// pairs).  For a block pair (I, J):
+//   1. G = [W_I W_J]^T [W_I W_J]   (W2 x W2 Gram, FP32 (or FP64) FMA, rows streamed
+//      through shared memory in chunks);
+//   2. if some |g_ij| > tol sqrt(g_ii g_jj): one cyclic sweep of two-sided Jacobi on G
+//      (round-robin over all W2 (W2-1)/2 pairs, rotation angle and convergence test in
+//      FP64, G and the accumulated rotation Q updated in the storage precision);
+//   3. [W_I W_J] <- [W_I W_J] Q and [V_I V_J] <- [V_I V_J] Q.
+// A column pair is rotated exactly as in the scalar method: zeta = (b - a) / (2 g),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t,
+// w_i' = c w_i - s w_j, w_j' = s w_i + c w_j.  A slice has converged after a sweep in
+// which no block pair needed a rotation (the scalar stopping rule, applied to Grams
+// formed fresh from the current columns).
+//
+// GB300 mapping: a thread-block cluster of CL CTAs owns one slice at a time (CTAs of a
+// cluster are co-scheduled, so the per-round barrier.cluster is safe); CTA r takes block
+// pairs r, r+CL, ... of each round.  The slice and its V stay in global memory, which is
+// L2-resident because only (clusters in flight) slices are live at once; global loads
+// bypass L1 (ld.global.cg) because other CTAs of the cluster rewrite the columns
+// between rounds.  Clusters are persistent and pull slice indices from an atomic
+// counter.  Every loop is bounded (sweep cap), and no device code traps.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace tsvdm {
+namespace {
+
+constexpr int NT = 256;
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
+template <typename T, int W2>
+struct Cfg {
+  static constexpr int B = W2 / 2;                    // block width
+  static constexpr int RC = (W2 >= 64) ? 64 : 128;    // rows per streamed chunk
+  static constexpr int VN = Vec16<T>::N;
+  static constexpr int LDR = RC + VN;                 // chunk column stride (elements)
+  static constexpr int TD = W2 / 4;                   // Gram tiles per dimension
+  static constexpr int TILES = TD * TD;
+  static constexpr int KG = NT / TILES;               // Gram K-groups
+  static constexpr int CPW = W2 / 8;                  // apply: columns per warp
+  static constexpr int RPT = RC / 32;                 // apply: rows per thread
+  static constexpr int LDG = W2 + 1;                  // Gram stride
+  static constexpr int CHUNK = W2 * LDR;
+  static constexpr int GPART = KG * W2 * W2;
+  static constexpr int BUF = CHUNK > GPART ? CHUNK : GPART;
+  static_assert(NT % TILES == 0, "tiles must divide the block");
+  static_assert(RC % (KG * VN) == 0, "K-groups must tile the chunk");
+};
+
+__device__ __forceinline__ void rr_pair(int n, int round, int q, int &a, int &b) {
+  // circle method: players 0..n-1 (n even), rounds 0..n-2, pairs q = 0..n/2-1
+  if (q == 0) {
+    a = n - 1;
+    b = round;
+  } else {
+    a = (round + q) % (n - 1);
+    b = (round - q + (n - 1)) % (n - 1);
+  }
+  if (a > b) {
+    int t = a;
+    a = b;
+    b = t;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+template <typename T, int W2>
+struct Smem {
+  T buf[Cfg<T, W2>::BUF];            // streamed chunk / Gram partials
+  T G[W2 * Cfg<T, W2>::LDG];         // Gram matrix
+  T Q[W2 * W2];                      // accumulated rotation, Q[c*W2 + j]
+  T cs[W2];                          // c, s per pair of the current step
+  T dd[W2];                          // updated diagonal per pair
+  int pi[W2 / 2], pj[W2 / 2];
+  int rot[W2 / 2];
+  int col[W2];                       // global column of local column c (-1 = padding)
+  int any_rot;                       // this block pair rotated
+  int sweep_any;                     // this CTA rotated in this sweep
+  int nonfinite;
+  long long nrot;
+  int slice[2];
+  int vote[2];
+};
+
+// Gram G = Wc^T Wc for the W2 columns of the block pair (columns col[]).
+template <typename T, int W2>
+__device__ void gram(Smem<T, W2> &s, const T *__restrict__ Wsl, int rows, int lda) {
+  using C = Cfg<T, W2>;
+  using V = typename Vec16<T>::type;
+  const int tid = threadIdx.x;
+  const int kg = tid / C::TILES;
+  const int tile = tid % C::TILES;
+  const int ti = tile / C::TD, tj = tile % C::TD;
+  T acc[4][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) acc[e][f] = T(0);
+  T *ch = s.buf;
+  for (int r0 = 0; r0 < rows; r0 += C::RC) {
+    for (int idx = tid; idx < W2 * C::RC; idx += NT) {
+      int c = idx / C::RC, r = idx % C::RC;
+      int gc = s.col[c];
+      T v = T(0);
+      if (gc >= 0 && r0 + r < rows) v = ldcg(Wsl + (int64_t)gc * lda + r0 + r);
+      ch[c * C::LDR + r] = v;
+    }
+    __syncthreads();
+    for (int r = kg * C::VN; r < C::RC; r += C::KG * C::VN) {
+      T a[4][C::VN], b[4][C::VN];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        V va = *reinterpret_cast<const V *>(ch + (ti + C::TD * e) * C::LDR + r);
+        V vb = *reinterpret_cast<const V *>(ch + (tj + C::TD * e) * C::LDR + r);
+        const T *pa = reinterpret_cast<const T *>(&va);
+        const T *pb = reinterpret_cast<const T *>(&vb);
+#pragma unroll
+        for (int u = 0; u < C::VN; ++u) {
+          a[e][u] = pa[u];
+          b[e][u] = pb[u];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < C::VN; ++u)
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) acc[e][f] = fma(a[e][u], b[f][u], acc[e][f]);
+    }
+    __syncthreads();
+  }
+  // reduce the K-groups in a fixed order
+  T *gp = s.buf;
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      gp[(kg * W2 + (ti + C::TD * e)) * W2 + (tj + C::TD * f)] = acc[e][f];
+  __syncthreads();
+  for (int idx = tid; idx < W2 * W2; idx += NT) {
+    int i = idx / W2, j = idx % W2;
+    T sum = T(0);
+    for (int g = 0; g < C::KG; ++g) sum += gp[(g * W2 + i) * W2 + j];
+    s.G[i * C::LDG + j] = sum;
+  }
+  __syncthreads();
+}
+
+// One cyclic two-sided Jacobi sweep on G, accumulating the rotations in Q.
+// Returns (in s.any_rot) whether any pair was rotated.
+template <typename T, int W2>
+__device__ void inner_sweep(Smem<T, W2> &s, double tol) {
+  using C = Cfg<T, W2>;
+  const int tid = threadIdx.x;
+  constexpr int NP = W2 / 2;
+  // fresh-Gram convergence test: does any pair exceed the threshold?
+  int need = 0;
+  for (int idx = tid; idx < W2 * W2; idx += NT) {
+    int i = idx / W2, j = idx % W2;
+    if (i < j) {
+      double a = (double)s.G[i * C::LDG + i], b = (double)s.G[j * C::LDG + j];
+      double g = (double)s.G[i * C::LDG + j];
+      if (isfinite(a) && isfinite(b) && fabs(g) > tol * sqrt(a * b)) need = 1;
+    }
+  }
+  if (tid == 0) s.any_rot = 0;
+  if (!__syncthreads_or(need)) return;
+  for (int idx = tid; idx < W2 * W2; idx += NT) s.Q[idx] = (idx / W2 == idx % W2) ? T(1) : T(0);
+  __syncthreads();
+  for (int step = 0; step < W2 - 1; ++step) {
+    if (tid < NP) {
+      int i, j;
+      rr_pair(W2, step, tid, i, j);
+      s.pi[tid] = i;
+      s.pj[tid] = j;
+      double a = (double)s.G[i * C::LDG + i];
+      double b = (double)s.G[j * C::LDG + j];
+      double g = (double)s.G[i * C::LDG + j];
+      int rot = 0;
+      if (!(isfinite(a) && isfinite(b))) {
+        s.nonfinite = 1;
+      } else if (fabs(g) > tol * sqrt(a * b)) {
+        double zeta = (b - a) / (2.0 * g);
+        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        s.cs[2 * tid] = (T)c;
+        s.cs[2 * tid + 1] = (T)(c * t);
+        s.dd[2 * tid] = (T)(a - t * g);
+        s.dd[2 * tid + 1] = (T)(b + t * g);
+        rot = 1;
+        s.any_rot = 1;
+      }
+      if (!rot) {
+        s.cs[2 * tid] = T(1);
+        s.cs[2 * tid + 1] = T(0);
+      }
+      s.rot[tid] = rot;
+    }
+    __syncthreads();
+    // G <- J^T G J, block by block (blocks of this step's pairs partition G)
+    for (int blk = tid; blk < NP * NP; blk += NT) {
+      int pp = blk / NP, qq = blk % NP;
+      int rp = s.rot[pp], rq = s.rot[qq];
+      if (!(rp | rq)) continue;
+      int i1 = s.pi[pp], j1 = s.pj[pp], i2 = s.pi[qq], j2 = s.pj[qq];
+      if (pp == qq) {
+        s.G[i1 * C::LDG + i1] = s.dd[2 * pp];
+        s.G[j1 * C::LDG + j1] = s.dd[2 * pp + 1];
+        s.G[i1 * C::LDG + j1] = T(0);
+        s.G[j1 * C::LDG + i1] = T(0);
+        continue;
+      }
+      T c1 = s.cs[2 * pp], s1 = s.cs[2 * pp + 1];
+      T c2 = s.cs[2 * qq], s2 = s.cs[2 * qq + 1];
+      T b00 = s.G[i1 * C::LDG + i2], b01 = s.G[i1 * C::LDG + j2];
+      T b10 = s.G[j1 * C::LDG + i2], b11 = s.G[j1 * C::LDG + j2];
+      // rows (J_p^T)
+      T r00 = c1 * b00 - s1 * b10, r01 = c1 * b01 - s1 * b11;
+      T r10 = s1 * b00 + c1 * b10, r11 = s1 * b01 + c1 * b11;
+      // columns (J_q)
+      s.G[i1 * C::LDG + i2] = c2 * r00 - s2 * r01;
+      s.G[i1 * C::LDG + j2] = s2 * r00 + c2 * r01;
+      s.G[j1 * C::LDG + i2] = c2 * r10 - s2 * r11;
+      s.G[j1 * C::LDG + j2] = s2 * r10 + c2 * r11;
+    }
+    // Q <- Q J
+    for (int it = tid; it < W2 * NP; it += NT) {
+      int qq = it / W2, r = it % W2;
+      if (!s.rot[qq]) continue;
+      int i = s.pi[qq], j = s.pj[qq];
+      T c = s.cs[2 * qq], sn = s.cs[2 * qq + 1];
+      T x = s.Q[r * W2 + i], y = s.Q[r * W2 + j];
+      s.Q[r * W2 + i] = c * x - sn * y;
+      s.Q[r * W2 + j] = sn * x + c * y;
+    }
+    if (tid < NP && s.rot[tid]) atomicAdd((unsigned long long *)&s.nrot, 1ull);
+    __syncthreads();
+  }
+}
+
+// [Wsl(:, col)] <- [Wsl(:, col)] Q, streamed over row chunks.
+template <typename T, int W2>
+__device__ void apply_q(Smem<T, W2> &s, T *__restrict__ Wsl, int rows, int lda) {
+  using C = Cfg<T, W2>;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  T *ch = s.buf;
+  for (int r0 = 0; r0 < rows; r0 += C::RC) {
+    for (int idx = tid; idx < W2 * C::RC; idx += NT) {
+      int c = idx / C::RC, r = idx % C::RC;
+      int gc = s.col[c];
+      T v = T(0);
+      if (gc >= 0 && r0 + r < rows) v = ldcg(Wsl + (int64_t)gc * lda + r0 + r);
+      ch[c * C::LDR + r] = v;
+    }
+    __syncthreads();
+    T acc[C::RPT][C::CPW];
+#pragma unroll
+    for (int q = 0; q < C::RPT; ++q)
+#pragma unroll
+      for (int e = 0; e < C::CPW; ++e) acc[q][e] = T(0);
+    const int j0 = warp * C::CPW;
+#pragma unroll 4
+    for (int c = 0; c < W2; ++c) {
+      T qv[C::CPW];
+#pragma unroll
+      for (int e = 0; e < C::CPW; ++e) qv[e] = s.Q[c * W2 + j0 + e];
+#pragma unroll
+      for (int q = 0; q < C::RPT; ++q) {
+        T a = ch[c * C::LDR + lane + 32 * q];
+#pragma unroll
+        for (int e = 0; e < C::CPW; ++e) acc[q][e] = fma(a, qv[e], acc[q][e]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < C::CPW; ++e) {
+      int gc = s.col[j0 + e];
+      if (gc < 0) continue;
+#pragma unroll
+      for (int q = 0; q < C::RPT; ++q) {
+        int r = r0 + lane + 32 * q;
+        if (r < rows) __stcg(Wsl + (int64_t)gc * lda + r, acc[q][e]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int W2>
+__global__ void __launch_bounds__(NT) jacobi_kernel(JacobiParams p) {
+  using C = Cfg<T, W2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<T, W2> &s = *reinterpret_cast<Smem<T, W2> *>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int csize = (int)cluster.num_blocks();
+  const int tid = threadIdx.x;
+  const int rows = p.rows, cols = p.cols;
+  int nb = (cols + C::B - 1) / C::B;
+  if (nb & 1) ++nb;
+  if (nb < 2) nb = 2;
+  const double tol = p.tol;
+
+  for (int iter = 0;; ++iter) {
+    const int par = iter & 1;
+    if (crank == 0 && tid == 0) s.slice[par] = atomicAdd(p.queue, 1);
+    cluster.sync();
+    const int slice = *cluster.map_shared_rank(&s.slice[par], 0);
+    if (slice >= p.nslices) break;
+    T *Wsl = reinterpret_cast<T *>(p.A) + (int64_t)slice * p.sA;
+    T *Vsl = reinterpret_cast<T *>(p.V) + (int64_t)slice * p.sV;
+
+    // V = I (this CTA initialises columns crank, crank + csize, ...)
+    for (int c = crank; c < cols; c += csize)
+      for (int r = tid; r < cols; r += NT) __stcg(Vsl + (int64_t)c * cols + r, r == c ? T(1) : T(0));
+    if (tid == 0) {
+      s.nrot = 0;
+      s.nonfinite = 0;
+    }
+    cluster.sync();
+
+    int converged = 0, sweep = 0;
+    for (sweep = 1; sweep <= p.max_sweeps; ++sweep) {
+      if (tid == 0) s.sweep_any = 0;
+      for (int round = 0; round < nb - 1; ++round) {
+        for (int q = crank; q < nb / 2; q += csize) {
+          int bi, bj;
+          rr_pair(nb, round, q, bi, bj);
+          if (tid < W2) {
+            int gc = (tid < C::B) ? bi * C::B + tid : bj * C::B + (tid - C::B);
+            s.col[tid] = gc < cols ? gc : -1;
+          }
+          __syncthreads();
+          gram<T, W2>(s, Wsl, rows, rows);
+          inner_sweep<T, W2>(s, tol);
+          if (s.any_rot) {
+            if (tid == 0) s.sweep_any = 1;
+            apply_q<T, W2>(s, Wsl, rows, rows);
+            apply_q<T, W2>(s, Vsl, cols, cols);
+          }
+          __syncthreads();
+        }
+        __threadfence();
+        cluster.sync();
+      }
+      // cluster-wide vote: did anybody rotate during this sweep?
+      if (tid == 0) s.vote[sweep & 1] = s.sweep_any;
+      cluster.sync();
+      int any = 0;
+      for (int r = 0; r < csize; ++r) any |= *cluster.map_shared_rank(&s.vote[sweep & 1], r);
+      if (!any) {
+        converged = 1;
+        break;
+      }
+    }
+    if (tid == 0) {
+      atomicAdd((unsigned long long *)&p.rots[slice], (unsigned long long)s.nrot);
+      if (s.nonfinite) atomicOr(p.status, ST_NONFINITE);
+      if (crank == 0) {
+        p.sweeps[slice] = converged ? sweep : -1;
+        if (!converged) atomicOr(p.status, ST_NOCONV);
+      }
+    }
+  }
+  cluster.sync();  // keep shared memory alive until every CTA has read the slice index
+}
+
+template <typename T, int W2>
+cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hint,
+                          int grid_hint) {
+  auto kern = jacobi_kernel<T, W2>;
+  size_t smem = sizeof(Smem<T, W2>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  int nb = (p.cols + W2 / 2 - 1) / (W2 / 2);
+  if (nb & 1) ++nb;
+  if (nb < 2) nb = 2;
+  int cl = 1;
+  int want = cluster_hint > 0 ? cluster_hint : 16;
+  while (cl * 2 <= want && cl * 2 <= nb / 2) cl *= 2;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int max_clusters = 0;
+  for (;;) {
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cl);
+    e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
+    if (e == cudaSuccess && max_clusters > 0) break;
+    cudaGetLastError();
+    if (cl == 1) return e == cudaSuccess ? cudaErrorInvalidConfiguration : e;
+    cl /= 2;
+  }
+  // Limit the slices in flight so their working set (W and V) stays in L2.
+  double slice_bytes = (double)sizeof(T) * ((double)p.rows * p.cols + (double)p.cols * p.cols);
+  int l2_clusters = (int)(64.0 * 1024 * 1024 / (slice_bytes > 1 ? slice_bytes : 1));
+  int nclusters = max_clusters;
+  if (grid_hint > 0) nclusters = grid_hint;
+  else if (l2_clusters < nclusters) nclusters = l2_clusters > 0 ? l2_clusters : 1;
+  if (nclusters > p.nslices) nclusters = p.nslices;
+  if (nclusters < 1) nclusters = 1;
+  cfg.gridDim = dim3(nclusters * cl);
+  return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+// ---------------------------------------------------------------- finalize
+// sigma_j = ||w_j|| and a stable descending order (ties: lower column first).
+template <typename T>
+__global__ void __launch_bounds__(256) finalize_kernel(const T *__restrict__ A, int64_t sA,
+                                                       int rows, int cols, T *sig, int *perm,
+                                                       int p2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *key = reinterpret_cast<T *>(smem_raw);
+  int *idx = reinterpret_cast<int *>(key + p2);
+  const int slice = blockIdx.x;
+  const T *W = A + (int64_t)slice * sA;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j < p2; j += 8) {
+    T acc = T(0);
+    if (j < cols)
+      for (int r = lane; r < rows; r += 32) {
+        T v = W[(int64_t)j * rows + r];
+        acc = fma(v, v, acc);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      key[j] = j < cols ? sqrt(acc) : T(-1);
+      idx[j] = j;
+    }
+  }
+  __syncthreads();
+  // bitonic sort: descending key, ascending index on ties
+  for (int k = 2; k <= p2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < p2; t += blockDim.x) {
+        int u = t ^ j;
+        if (u > t) {
+          bool up = ((t & k) == 0);
+          T kt = key[t], ku = key[u];
+          int it = idx[t], iu = idx[u];
+          bool t_first = (kt > ku) || (kt == ku && it < iu);   // t precedes u in output
+          if (up ? !t_first : t_first) {
+            key[t] = ku; key[u] = kt;
+            idx[t] = iu; idx[u] = it;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+    sig[(int64_t)slice * cols + j] = key[j];
+    perm[(int64_t)slice * cols + j] = idx[j];
+  }
+}
+
+// ---------------------------------------------------------------- emit
+// (bv, bi) <- the larger magnitude, first index on ties; bv starts at -1 (empty).
+template <typename T>
+__device__ __forceinline__ void merge_max(T a, int i, T &bv, int &bi) {
+  if (a > bv || (a == bv && i < bi)) {
+    bv = a;
+    bi = i;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void argmax_abs(T v, int i, T &bv, int &bi) { merge_max(fabs(v), i, bv, bi); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) emit_kernel(const T *__restrict__ A, int64_t sA,
+                                                   const T *__restrict__ Vw, int64_t sV,
+                                                   int rows, int cols, bool transposed,
+                                                   const T *__restrict__ sig,
+                                                   const int *__restrict__ perm,
+                                                   int64_t k_uniform, const int *ranks,
+                                                   const int64_t *offsets, T *U, T *S, T *V) {
+  const int q = blockIdx.x;
+  const int slice = blockIdx.y;
+  int64_t count = ranks ? (int64_t)ranks[slice] : k_uniform;
+  if (q >= count) return;
+  int64_t colbase = offsets ? offsets[slice] : (int64_t)slice * k_uniform;
+  const int j = perm[(int64_t)slice * cols + q];
+  const T sg = sig[(int64_t)slice * cols + q];
+  const T *wcol = A + (int64_t)slice * sA + (int64_t)j * rows;     // rows entries, scaled 1/sg
+  const T *zcol = Vw + (int64_t)slice * sV + (int64_t)j * cols;    // cols entries
+  const T inv = sg > T(0) ? T(1) / sg : T(0);
+  // left vector: W-part (non-transposed) or Z-part (transposed)
+  const int nl = transposed ? cols : rows;
+  const int nr = transposed ? rows : cols;
+  __shared__ T sbv[8];
+  __shared__ int sbi[8];
+  __shared__ T s_sign;
+  T bv = T(-1);
+  int bi = 0x7fffffff;
+  for (int a = threadIdx.x; a < nl; a += blockDim.x) {
+    T v = transposed ? zcol[a] : wcol[a] * inv;
+    argmax_abs(v, a, bv, bi);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    merge_max(ov, oi, bv, bi);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sbv[threadIdx.x >> 5] = bv;
+    sbi[threadIdx.x >> 5] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T b = T(-1);
+    int i = 0x7fffffff;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) merge_max(sbv[w], sbi[w], b, i);
+    T ref;
+    if (b > T(0)) {
+      ref = transposed ? zcol[i] : wcol[i] * inv;
+    } else {
+      // zero left vector: take the sign from the right vector
+      T b2 = T(-1);
+      int i2 = 0x7fffffff;
+      for (int a = 0; a < nr; ++a) argmax_abs(transposed ? wcol[a] * inv : zcol[a], a, b2, i2);
+      ref = b2 > T(0) ? (transposed ? wcol[i2] * inv : zcol[i2]) : T(1);
+    }
+    s_sign = ref < T(0) ? T(-1) : T(1);
+    S[colbase + q] = sg;
+  }
+  __syncthreads();
+  const T sgn = s_sign;
+  const int64_t n1 = nl, n2 = nr;
+  T *Ucol = U + (colbase + q) * n1;
+  T *Vcol = V + (colbase + q) * n2;
+  for (int a = threadIdx.x; a < nl; a += blockDim.x)
+    Ucol[a] = sgn * (transposed ? zcol[a] : wcol[a] * inv);
+  for (int b = threadIdx.x; b < nr; b += blockDim.x)
+    Vcol[b] = sgn * (transposed ? wcol[b] * inv : zcol[b]);
+}
+
+template <typename T>
+__global__ void transpose_kernel(const T *__restrict__ A, int64_t m, int64_t p, T *__restrict__ B) {
+  __shared__ T tile[32][33];
+  const int64_t slice = blockIdx.z;
+  const T *a = A + slice * m * p;
+  T *b = B + slice * m * p;
+  int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    int64_t i = i0 + threadIdx.x, j = j0 + y;
+    if (i < m && j < p) tile[y][threadIdx.x] = a[i + m * j];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    int64_t j = j0 + threadIdx.x, i = i0 + y;
+    if (i < m && j < p) b[j + p * i] = tile[threadIdx.x][y];
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int cluster_hint, int grid_hint) {
+  if (p.cols <= 8) return launch_jacobi<T, 16>(p, st, cluster_hint, grid_hint);
+  if (p.cols <= 16) return launch_jacobi<T, 32>(p, st, cluster_hint, grid_hint);
+  return launch_jacobi<T, 32>(p, st, cluster_hint, grid_hint);
+}
+
+template <typename T>
+cudaError_t jacobi_finalize(const T *A, int64_t sA, int rows, int cols, int nslices, T *sig,
+                            int *perm, cudaStream_t st) {
+  int p2 = 1;
+  while (p2 < cols) p2 <<= 1;
+  size_t smem = (size_t)p2 * (sizeof(T) + sizeof(int));
+  auto kern = finalize_kernel<T>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<nslices, 256, smem, st>>>(A, sA, rows, cols, sig, perm, p2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t emit_factors(const T *A, int64_t sA, const T *Vw, int64_t sV, int rows, int cols,
+                         int nslices, bool transposed, const T *sig, const int *perm,
+                         int64_t k_uniform, const int *ranks, const int64_t *offsets, T *U,
+                         T *S, T *V, cudaStream_t st) {
+  int gx = ranks ? cols : (int)k_uniform;
+  if (gx <= 0 || nslices <= 0) return cudaSuccess;
+  emit_kernel<T><<<dim3(gx, nslices), 256, 0, st>>>(A, sA, Vw, sV, rows, cols, transposed, sig,
+                                                    perm, k_uniform, ranks, offsets, U, S, V);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t transpose_slices(const T *A, int64_t m, int64_t p, int64_t nslices, T *B,
+                             cudaStream_t st) {
+  dim3 grid((unsigned)((m + 31) / 32), (unsigned)((p + 31) / 32), (unsigned)nslices);
+  transpose_kernel<T><<<grid, dim3(32, 8), 0, st>>>(A, m, p, B);
+  return cudaGetLastError();
+}
+
+#define INST(T)                                                                               \
+  template cudaError_t jacobi_run<T>(const JacobiParams &, cudaStream_t, int, int);           \
+  template cudaError_t jacobi_finalize<T>(const T *, int64_t, int, int, int, T *, int *,      \
+                                          cudaStream_t);                                      \
+  template cudaError_t emit_factors<T>(const T *, int64_t, const T *, int64_t, int, int, int, \
+                                       bool, const T *, const int *, int64_t, const int *,    \
+                                       const int64_t *, T *, T *, T *, cudaStream_t);         \
+  template cudaError_t transpose_slices<T>(const T *, int64_t, int64_t, int64_t, T *,         \
+                                           cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace tsvdm

@@ -1,0 +1,199 @@
+"""ctypes binding of libtsvdm.so (include/tsvdm.h), same names as the C entry points.
+
+Argument marshalling only: tensors are passed by data pointer, every computation runs in
+the library's CUDA kernels.  Loading fails loudly when the library has not been built
+(there is no CPU fallback).  PyTorch is used for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtsvdm.so")
+
+OK, EINVAL, ENOTORTHO, ENOCONV, ENONFINITE, ETIMEOUT, ENOMEM, ECAPACITY, ECUDA, ENOTSUP = range(10)
+F32, F64 = 0, 1
+P_FP64, P_FP32, P_TF32, P_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": P_FP64, "fp32": P_FP32, "tf32": P_TF32, "bf16x3": P_BF16X3}
+
+# every symbol include/tsvdm.h declares, with (restype, argtypes)
+_i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_pi64, _pdbl = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "tsvdm_plan_create": (_i32, [_i64, _i64, _i64, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "tsvdm_plan_destroy": (_i32, [_vp]),
+    "tsvdm_plan_set_jacobi": (_i32, [_vp, _dbl, _i32]),
+    "tsvdm_transform": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "tsvdm_fixed_rank": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pdbl]),
+    "tsvdm_tolerance": (_i32, [_vp, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _vp, _i64, _pi64, _pdbl]),
+    "tsvdm_tolerance_pack": (_i32, [_vp, _vp, _vp, _vp, _i64]),
+    "tsvdm_reconstruct": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "tsvdm_backward": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _dbl, _vp, _vp, _vp]),
+    "tsvdm_last_status": (_i32, [_vp]),
+    "tsvdm_plan_stats": (_i32, [_vp, _pi64, _pi64]),
+    "tsvdm_strerror": (ctypes.c_char_p, [_i32]),
+    "tsvdm_cayley": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tsvdm_cayley_backward": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tsvdm_plan_profile": (_i32, [_vp, _i32]),
+    "tsvdm_plan_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_float), _pi64]),
+    "tsvdm_adam": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _i64, _dbl, _dbl, _dbl, _dbl, _vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TsvdmError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = lib().tsvdm_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__("%s: %s (status %d)" % (where, msg, status))
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libtsvdm.so is not built (run __graft_entry__.build() or "
+                                   "python paper_2605_16058_gb300/build.py)")
+            h = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(h, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = h
+    return _lib
+
+
+def check(status, where):
+    if status != OK:
+        raise TsvdmError(status, where)
+    return status
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- thin wrappers
+def tsvdm_plan_create(n1, n2, n3, dtype, prec, m_is_orthogonal, stream=None):
+    h = ctypes.c_void_p()
+    check(lib().tsvdm_plan_create(n1, n2, n3, dtype, prec, int(bool(m_is_orthogonal)),
+                                  _stream(stream), ctypes.byref(h)), "tsvdm_plan_create")
+    return h
+
+
+def tsvdm_plan_destroy(plan):
+    return lib().tsvdm_plan_destroy(plan)
+
+
+def tsvdm_plan_set_jacobi(plan, tol, max_sweeps):
+    return check(lib().tsvdm_plan_set_jacobi(plan, float(tol), int(max_sweeps)),
+                 "tsvdm_plan_set_jacobi")
+
+
+def tsvdm_transform(plan, X, M, inverse, Y):
+    return check(lib().tsvdm_transform(plan, _ptr(X), _ptr(M), int(inverse), _ptr(Y)),
+                 "tsvdm_transform")
+
+
+def tsvdm_fixed_rank(plan, X, M, k, U, S, V, original_domain=0, want_rel_err=True,
+                     raise_on_error=True):
+    err = ctypes.c_double(math.nan)
+    st = lib().tsvdm_fixed_rank(plan, _ptr(X), _ptr(M), int(k), _ptr(U), _ptr(S), _ptr(V),
+                                int(original_domain), ctypes.byref(err) if want_rel_err else None)
+    if raise_on_error:
+        check(st, "tsvdm_fixed_rank")
+    return (err.value if want_rel_err else None), st
+
+
+def tsvdm_tolerance(plan, X, M, eps, ranks, offsets, U, S, V, capacity, want_rel_err=True,
+                    raise_on_error=True):
+    tot = ctypes.c_int64(0)
+    err = ctypes.c_double(math.nan)
+    st = lib().tsvdm_tolerance(plan, _ptr(X), _ptr(M), float(eps), _ptr(ranks), _ptr(offsets),
+                               _ptr(U), _ptr(S), _ptr(V), int(capacity), ctypes.byref(tot),
+                               ctypes.byref(err) if want_rel_err else None)
+    if raise_on_error and st not in (OK, ECAPACITY):
+        check(st, "tsvdm_tolerance")
+    return tot.value, (err.value if want_rel_err else None), st
+
+
+def tsvdm_tolerance_pack(plan, U, S, V, capacity):
+    return check(lib().tsvdm_tolerance_pack(plan, _ptr(U), _ptr(S), _ptr(V), int(capacity)),
+                 "tsvdm_tolerance_pack")
+
+
+def tsvdm_reconstruct(plan, U, S, V, offsets, k, M, Xk):
+    return check(lib().tsvdm_reconstruct(plan, _ptr(U), _ptr(S), _ptr(V), _ptr(offsets), int(k),
+                                         _ptr(M), _ptr(Xk)), "tsvdm_reconstruct")
+
+
+def tsvdm_backward(plan, X, M, k, U, S, V, dL, dX, dM, loss=None):
+    """loss: None, a 1-element float64 CUDA tensor (written without synchronising), or
+    'host' to return the value."""
+    if isinstance(loss, str):
+        out = ctypes.c_double(math.nan)
+        check(lib().tsvdm_backward(plan, _ptr(X), _ptr(M), int(k), _ptr(U), _ptr(S), _ptr(V),
+                                   float(dL), _ptr(dX), _ptr(dM), ctypes.byref(out)),
+              "tsvdm_backward")
+        return out.value
+    check(lib().tsvdm_backward(plan, _ptr(X), _ptr(M), int(k), _ptr(U), _ptr(S), _ptr(V),
+                               float(dL), _ptr(dX), _ptr(dM), _ptr(loss)), "tsvdm_backward")
+    return None
+
+
+def tsvdm_last_status(plan):
+    return lib().tsvdm_last_status(plan)
+
+
+def tsvdm_plan_stats(plan):
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    check(lib().tsvdm_plan_stats(plan, ctypes.byref(a), ctypes.byref(b)), "tsvdm_plan_stats")
+    return a.value, b.value
+
+
+STAGES = ("ttm", "transpose", "jacobi", "finalize", "select", "emit", "other")
+
+
+def tsvdm_plan_profile(plan, enable):
+    return check(lib().tsvdm_plan_profile(plan, int(enable)), "tsvdm_plan_profile")
+
+
+def tsvdm_plan_profile_read(plan):
+    ms = (ctypes.c_float * len(STAGES))()
+    n = ctypes.c_int64(0)
+    check(lib().tsvdm_plan_profile_read(plan, ms, ctypes.byref(n)), "tsvdm_plan_profile_read")
+    return dict(zip(STAGES, [float(x) for x in ms])), n.value
+
+
+def tsvdm_cayley(n, dtype, A, M0, M, Z, Q, work, stream=None):
+    return check(lib().tsvdm_cayley(int(n), dtype, _ptr(A), _ptr(M0), _ptr(M), _ptr(Z), _ptr(Q),
+                                    _ptr(work), _stream(stream)), "tsvdm_cayley")
+
+
+def tsvdm_cayley_backward(n, dtype, M0, Z, Q, dM, dA, work, stream=None):
+    return check(lib().tsvdm_cayley_backward(int(n), dtype, _ptr(M0), _ptr(Z), _ptr(Q), _ptr(dM),
+                                             _ptr(dA), _ptr(work), _stream(stream)),
+                 "tsvdm_cayley_backward")
+
+
+def tsvdm_adam(count, dtype, param, grad, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e-8,
+               stream=None):
+    return check(lib().tsvdm_adam(int(count), dtype, _ptr(param), _ptr(grad), _ptr(m1), _ptr(m2),
+                                  int(step), float(lr), float(beta1), float(beta2), float(eps),
+                                  _stream(stream)), "tsvdm_adam")

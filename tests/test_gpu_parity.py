@@ -1,0 +1,277 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element, on seeded
+inputs that span several tiles with ragged tails.
+
+Tolerances (stated per precision):
+  singular values   |s_gpu - s_oracle| <= 1e-5 sigma_max (FP32), 1e-12 sigma_max (FP64)
+  subspaces         ||U_k U_k^T - U~_k U~_k^T||_F <= 1e-4 where the gap at k exceeds
+                    1e-3 sigma_max (FP32) / 1e-6 sigma_max (FP64) (no sign ambiguity)
+  relative error    |rel_gpu - rel_oracle| <= 1e-5 (FP32), 1e-12 (FP64)
+  t-SVDM-II ranks   exact, except slices holding a sigma^2 within 1e-6 relative of tau
+  TTM               max |Y - Y_oracle| <= 2e-6 max|Y| (FP32), 1e-13 max|Y| (FP64)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_16058_gb300 import synth
+
+from helpers import np_lib, proj_diff, t_lib
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _need_gpu()
+    from paper_2605_16058_gb300 import build
+    build.build()
+
+
+def _plan(n1, n2, n3, dt, orthogonal=True):
+    from paper_2605_16058_gb300.tsvdm import Plan
+    return Plan(n1, n2, n3, dtype=dt, orthogonal=orthogonal)
+
+
+TOL = {torch.float32: dict(sig=1e-5, proj=1e-4, gap=1e-3, rel=1e-5, ttm=2e-6),
+       torch.float64: dict(sig=1e-12, proj=1e-9, gap=1e-6, rel=1e-12, ttm=1e-13)}
+
+
+def _rand(shape, seed, dtype=np.float64):
+    return np.random.default_rng(seed).standard_normal(shape).astype(dtype)
+
+
+# ---------------------------------------------------------------- TTM
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+@pytest.mark.parametrize("shape", [(37, 29, 19), (130, 3, 70), (1, 1, 1), (5, 7, 129)])
+def test_ttm_forward_and_inverse(dt, shape):
+    n1, n2, n3 = shape
+    X = _rand(shape, 1)
+    M = synth.haar_orthogonal(n3, np.random.default_rng(2)) * 1.5
+    plan = _plan(n1, n2, n3, dt)
+    Xd, Md = t_lib(X, dtype=dt), t_lib(M, dtype=dt)
+    Y = plan.transform(Xd, Md)
+    want = oracle.ttm3(X.astype(np.float32) if dt == torch.float32 else X,
+                       M.astype(np.float32) if dt == torch.float32 else M)
+    got = np_lib(Y)
+    assert np.max(np.abs(got - want)) <= TOL[dt]["ttm"] * max(np.max(np.abs(want)), 1e-30) * (n3 ** 0.5)
+    Xb = np_lib(plan.transform(Y, Md, inverse=True))     # M^{-1} = M^T / c^2
+    assert np.max(np.abs(Xb - X)) <= 50 * TOL[dt]["ttm"] * np.max(np.abs(X)) * n3 ** 0.5
+
+
+# ---------------------------------------------------------------- t-SVDM-I
+CASES_I = [
+    ("smoke", None, torch.float64, 8),
+    ("tall", (100, 37, 5), torch.float32, 6),
+    ("wide", (37, 100, 5), torch.float32, 6),
+    ("tiles", (200, 130, 3), torch.float32, 20),
+    ("tall64", (150, 70, 4), torch.float64, 10),
+    ("one_slice", (33, 20, 1), torch.float32, 20),
+    ("rankdef", (80, 40, 3), torch.float32, 4),
+]
+
+
+def _case_input(name, shape, seed=3):
+    if name == "smoke":
+        c = synth.smoke_case()
+        return c["X"], c["M"]
+    n1, n2, n3 = shape
+    rng = np.random.default_rng(seed)
+    if name == "rankdef":
+        X = synth.cp_tensor(n1, n2, n3, 5, rng, noise_rel=0.0)
+    else:
+        X = synth.cp_tensor(n1, n2, n3, min(n1, n2) // 2, rng, noise_rel=1e-2)
+    return X, synth.dct2_matrix(n3)
+
+
+def _compare_factors(dt, S_o, U_o, V_o, S_g, U_g, V_g, k):
+    tol = TOL[dt]
+    n3 = S_o.shape[1]
+    for i in range(n3):
+        so, sg = S_o[:, i], S_g[:, i]
+        smax = max(so[0], 1e-300)
+        assert np.max(np.abs(so[:k] - sg[:k])) <= tol["sig"] * smax, (i, so[:k], sg[:k])
+        for kk in range(1, k + 1):
+            gap_next = so[kk - 1] - so[kk] if kk < len(so) else so[kk - 1]
+            if gap_next > tol["gap"] * smax and so[kk - 1] > tol["gap"] * smax:
+                assert proj_diff(U_o[:, :kk, i], U_g[:, :kk, i]) <= tol["proj"], (i, kk)
+                assert proj_diff(V_o[:, :kk, i], V_g[:, :kk, i]) <= tol["proj"], (i, kk)
+
+
+@pytest.mark.parametrize("name,shape,dt,k", CASES_I, ids=[c[0] for c in CASES_I])
+def test_fixed_rank_matches_oracle(name, shape, dt, k):
+    X, M = _case_input(name, shape)
+    n1, n2, n3 = X.shape
+    if dt == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+        M = M.astype(np.float32).astype(np.float64)
+    ref = oracle.fixed_rank(X, M, k)
+    plan = _plan(n1, n2, n3, dt)
+    out = plan.fixed_rank(t_lib(X, dtype=dt), t_lib(M, dtype=dt), k)
+    U_g, S_g, V_g = np_lib(out["U"]), np_lib(out["S"]), np_lib(out["V"])
+    assert U_g.shape == (n1, k, n3) and S_g.shape == (k, n3) and V_g.shape == (n2, k, n3)
+    full = oracle.svd_slices(ref["Ahat"])
+    _compare_factors(dt, ref["S_all"], full[0], full[2], S_g, U_g, V_g, k)
+    assert abs(out["rel_err"] - ref["rel_err"]) <= TOL[dt]["rel"]
+    # left vectors orthonormal per slice
+    for i in range(n3):
+        nz = S_g[:, i] > 1e-6 * max(S_g[0, i], 1e-300)
+        u = U_g[:, nz, i]
+        assert np.linalg.norm(u.T @ u - np.eye(u.shape[1])) < (1e-4 if dt == torch.float32 else 1e-10)
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+def test_reconstruct_matches_oracle(dt):
+    X, M = _case_input("tall", (100, 37, 5))
+    n1, n2, n3 = X.shape
+    k = 7
+    plan = _plan(n1, n2, n3, dt)
+    Md = t_lib(M, dtype=dt)
+    out = plan.fixed_rank(t_lib(X, dtype=dt), Md, k)
+    Xk = np_lib(plan.reconstruct(out["U"], out["S"], out["V"], Md, k=k))
+    U, S, V = np_lib(out["U"]), np_lib(out["S"]), np_lib(out["V"])
+    want = oracle.reconstruct(U, S, V, M.T)
+    assert np.max(np.abs(Xk - want)) <= 1e-5 * np.max(np.abs(want)) * (1 if dt == torch.float32 else 1e-7)
+    # Eckart-Young: the direct error equals the reported one
+    direct = oracle.rel_err_direct(X, Xk)
+    assert abs(direct - out["rel_err"]) <= (2e-5 if dt == torch.float32 else 1e-11)
+
+
+def test_original_domain_factors():
+    X, M = _case_input("tall", (60, 30, 6))
+    n1, n2, n3 = X.shape
+    k = 5
+    plan = _plan(n1, n2, n3, torch.float64)
+    Md = t_lib(M, dtype=torch.float64)
+    hat = plan.fixed_rank(t_lib(X, dtype=torch.float64), Md, k)
+    org = plan.fixed_rank(t_lib(X, dtype=torch.float64), Md, k, original_domain=True)
+    for key in ("U", "S", "V"):
+        assert np.allclose(oracle.original_domain(np_lib(hat[key]), M.T), np_lib(org[key]), atol=1e-12)
+
+
+# ---------------------------------------------------------------- t-SVDM-II
+def _tie_slices(S, tau, rel=1e-6):
+    if not np.isfinite(tau) or tau <= 0:
+        return set()
+    near = np.abs(S * S - tau) <= rel * tau
+    return set(np.nonzero(near.any(axis=0))[0])
+
+
+@pytest.mark.parametrize("dt,shape,eps", [(torch.float64, (64, 48, 16), 0.05),
+                                          (torch.float32, (90, 60, 12), 0.02),
+                                          (torch.float32, (40, 70, 9), 0.1),
+                                          (torch.float64, (50, 30, 7), 1e-9)])
+def test_tolerance_matches_oracle(dt, shape, eps):
+    n1, n2, n3 = shape
+    rng = np.random.default_rng(7)
+    X = synth.cp_tensor(n1, n2, n3, min(n1, n2) // 3, rng, noise_rel=1e-2)
+    M = synth.dct2_matrix(n3)
+    if dt == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+        M = M.astype(np.float32).astype(np.float64)
+    ref = oracle.tolerance(X, M, eps)
+    plan = _plan(n1, n2, n3, dt)
+    out = plan.tolerance(t_lib(X, dtype=dt), t_lib(M, dtype=dt), eps)
+    ranks = out["ranks"].cpu().numpy()
+    off = out["offsets"].cpu().numpy()
+    assert off[0] == 0 and np.array_equal(np.diff(off), ranks) and off[-1] == out["total_rank"]
+    ties = _tie_slices(ref["S_all"], ref["tau"])
+    for i in range(n3):
+        if i not in ties:
+            assert ranks[i] == ref["ranks"][i], (i, ranks[i], ref["ranks"][i])
+    assert abs(out["rel_err"] - ref["rel_err"]) <= TOL[dt]["rel"] * 10
+    assert out["rel_err"] < eps or out["total_rank"] == n3 * min(n1, n2)
+    # packed factors: slice i's columns hold its leading rho_i triplets
+    U = out["U"].cpu().double().numpy().T
+    S = out["S"].cpu().double().numpy()
+    V = out["V"].cpu().double().numpy().T
+    full = oracle.svd_slices(ref["Ahat"])
+    for i in range(n3):
+        a, b = off[i], off[i + 1]
+        if b == a:
+            continue
+        smax = ref["S_all"][0, i]
+        assert np.max(np.abs(S[a:b] - ref["S_all"][: b - a, i])) <= TOL[dt]["sig"] * max(smax, 1e-300) * 10
+        kk = b - a
+        so = ref["S_all"][:, i]
+        if kk == len(so) or so[kk - 1] - so[kk] > TOL[dt]["gap"] * smax:
+            assert proj_diff(full[0][:, :kk, i], U[:, a:b]) <= TOL[dt]["proj"]
+
+
+def test_tolerance_ranks_equal_algorithm2_on_gpu_sigma():
+    """Integer decision taken in FP64 on both sides: Algorithm 2 of the oracle applied to
+    the GPU's own singular values reproduces the GPU's ranks exactly."""
+    n1, n2, n3 = 120, 80, 24
+    X = synth.climate(shape=(n1, n2, n3), seed=5)
+    M = synth.dct2_matrix(n3)
+    plan = _plan(n1, n2, n3, torch.float32)
+    for eps in (1e-3, 1e-2, 5e-2, 0.2):
+        out = plan.tolerance(t_lib(X), t_lib(M, dtype=torch.float32), eps)
+        f = plan.fixed_rank(t_lib(X), t_lib(M, dtype=torch.float32), min(n1, n2), rel_err=False)
+        S_gpu = np_lib(f["S"])
+        sel = oracle.select_ranks(S_gpu, eps)
+        assert np.array_equal(out["ranks"].cpu().numpy(), sel["ranks"])
+
+
+# ---------------------------------------------------------------- status paths
+def test_sweep_cap_reports_nonconvergence():
+    from paper_2605_16058_gb300 import native
+    X = _rand((64, 40, 3), 9, np.float32)
+    plan = _plan(64, 40, 3, torch.float32)
+    plan.set_jacobi(0.0, 1)
+    out = plan.fixed_rank(t_lib(X), t_lib(np.eye(3), dtype=torch.float32), 4, raise_on_error=False)
+    assert out["status"] == native.ENOCONV
+    plan.set_jacobi(0.0, 0)
+    out = plan.fixed_rank(t_lib(X), t_lib(np.eye(3), dtype=torch.float32), 4)
+    assert out["status"] == native.OK
+
+
+def test_nonfinite_input_is_reported():
+    from paper_2605_16058_gb300 import native
+    X = _rand((32, 20, 2), 10, np.float32)
+    X[3, 4, 1] = np.nan
+    plan = _plan(32, 20, 2, torch.float32)
+    out = plan.fixed_rank(t_lib(X), t_lib(np.eye(2), dtype=torch.float32), 3, raise_on_error=False)
+    assert out["status"] == native.ENONFINITE
+
+
+def test_host_buffers_match_device_buffers():
+    from paper_2605_16058_gb300 import native
+    X, M = _case_input("tall", (70, 50, 6))
+    Xf = X.astype(np.float32)
+    plan = _plan(70, 50, 6, torch.float32)
+    dev = plan.fixed_rank(t_lib(Xf), t_lib(M, dtype=torch.float32), 5)
+    Xh = t_lib(Xf, device="cpu").pin_memory()
+    Mh = t_lib(M, device="cpu", dtype=torch.float32)
+    U = torch.empty(6, 5, 70).pin_memory()
+    S = torch.empty(6, 5)
+    V = torch.empty(6, 5, 50)
+    err, st = native.tsvdm_fixed_rank(plan.handle, Xh, Mh, 5, U, S, V, 0, True)
+    assert st == native.OK
+    assert torch.equal(S, dev["S"].cpu()) and torch.equal(U, dev["U"].cpu())
+    assert err == dev["rel_err"]
+
+
+def test_zero_tensor_tolerance_keeps_nothing():
+    plan = _plan(20, 10, 4, torch.float32)
+    out = plan.tolerance(torch.zeros(4 * 10 * 20, device="cuda"), t_lib(synth.dct2_matrix(4), dtype=torch.float32), 0.1)
+    assert out["total_rank"] == 0 and out["rel_err"] == 0.0
+
+
+def test_argument_errors():
+    from paper_2605_16058_gb300 import native
+    plan = _plan(20, 10, 4, torch.float32, orthogonal=False)
+    X = torch.zeros(800, device="cuda")
+    M = torch.eye(4, device="cuda")
+    with pytest.raises(native.TsvdmError) as e:
+        plan.tolerance(X, M, 0.1)
+    assert e.value.status == native.ENOTORTHO
+    with pytest.raises(native.TsvdmError) as e:
+        plan.fixed_rank(X, M, 11)
+    assert e.value.status == native.EINVAL
