@@ -96,6 +96,13 @@ tsvdm_status tsvdm_plan_destroy(tsvdm_plan plan);
  * is still rotating after max_sweeps sets TSVDM_ENOCONV. */
 tsvdm_status tsvdm_plan_set_jacobi(tsvdm_plan plan, double tol, int max_sweeps);
 
+/* Launch shape of the batched Jacobi kernel (for tuning; 0 = automatic).  block_width:
+ * columns of a block pair (16, 32 or 64); cluster_size: CTAs that share one slice
+ * (1..16, powers of two, capped by the block pairs of a round and by the device);
+ * clusters: clusters launched (slices in flight).  EINVAL for other values. */
+tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster_size,
+                                   int clusters);
+
 /* Y = X x_3 M (inverse = 0) or Y = X x_3 M^{-1} (inverse = 1), Sec. 2.1.  For
  * inverse = 1 on an orthogonal plan, M is the forward matrix and M^T / c^2 is applied;
  * on a non-orthogonal plan, M must already hold M^{-1}.  X, Y: n1 x n2 x n3 device,

@@ -38,7 +38,7 @@ struct tsvdm_plan_s {
   size_t splitk_elems = 0;
   double tol = 0.0;
   int max_sweeps = 40;
-  int cluster_hint = 0, grid_hint = 0;
+  int width_hint = 0, cluster_hint = 0, grid_hint = 0;
   int tol_valid = 0;
   int64_t tol_total = 0;
   void *stage[STG_COUNT] = {};
@@ -178,7 +178,7 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   jp.sweeps = p->sweeps;
   jp.rots = p->rots;
   stage_begin(p, TSVDM_STAGE_JACOBI);
-  CK(jacobi_run<T>(jp, p->st, p->cluster_hint, p->grid_hint));
+  CK(jacobi_run<T>(jp, p->st, p->width_hint, p->cluster_hint, p->grid_hint));
   stage_end(p, TSVDM_STAGE_JACOBI, 1);
   stage_begin(p, TSVDM_STAGE_FINALIZE);
   CK(jacobi_finalize<T>((const T *)work_matrix(p), jp.sA, jp.rows, jp.cols, jp.nslices,
@@ -456,6 +456,18 @@ tsvdm_status tsvdm_plan_set_jacobi(tsvdm_plan plan, double tol, int max_sweeps) 
   if (!valid_plan(plan)) return TSVDM_EINVAL;
   plan->tol = tol > 0 ? tol : 0.0;
   plan->max_sweeps = max_sweeps > 0 ? max_sweeps : 40;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster_size,
+                                   int clusters) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  if (block_width != 0 && block_width != 16 && block_width != 32 && block_width != 64)
+    return TSVDM_EINVAL;
+  if (cluster_size < 0 || cluster_size > 16 || clusters < 0) return TSVDM_EINVAL;
+  plan->width_hint = block_width;
+  plan->cluster_hint = cluster_size;
+  plan->grid_hint = clusters;
   return TSVDM_OK;
 }
 

@@ -59,7 +59,8 @@ struct JacobiParams {
 };
 
 template <typename T>
-cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int cluster_hint, int grid_hint);
+cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, int cluster_hint,
+                       int grid_hint);
 
 // sigma (sorted descending) and the column permutation of each slice.
 template <typename T>

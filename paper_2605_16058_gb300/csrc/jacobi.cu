@@ -42,7 +42,8 @@ template <> struct Vec16<double> { using type = double2; static constexpr int N 
 template <typename T, int W2>
 struct Cfg {
   static constexpr int B = W2 / 2;                    // block width
-  static constexpr int RC = (W2 >= 64) ? 64 : 128;    // rows per streamed chunk
+  static constexpr int RC = 4096 / W2;                // rows per pipelined chunk
+  static constexpr int NS = 3;                        // pipeline stages
   static constexpr int VN = Vec16<T>::N;
   static constexpr int LDR = RC + VN;                 // chunk column stride (elements)
   static constexpr int TD = W2 / 4;                   // Gram tiles per dimension
@@ -53,9 +54,10 @@ struct Cfg {
   static constexpr int LDG = W2 + 1;                  // Gram stride
   static constexpr int CHUNK = W2 * LDR;
   static constexpr int GPART = KG * W2 * W2;
-  static constexpr int BUF = CHUNK > GPART ? CHUNK : GPART;
+  static constexpr int BUF = NS * CHUNK > GPART ? NS * CHUNK : GPART;
   static_assert(NT % TILES == 0, "tiles must divide the block");
   static_assert(RC % (KG * VN) == 0, "K-groups must tile the chunk");
+  static_assert(RC % 32 == 0, "apply rows");
 };
 
 __device__ __forceinline__ void rr_pair(int n, int round, int q, int &a, int &b) {
@@ -81,7 +83,7 @@ template <typename T, int W2>
 struct Smem {
   T buf[Cfg<T, W2>::BUF];            // streamed chunk / Gram partials
   T G[W2 * Cfg<T, W2>::LDG];         // Gram matrix
-  T Q[W2 * W2];                      // accumulated rotation, Q[c*W2 + j]
+  T Q[W2 * W2];                      // accumulated rotation, Q(r, j) at Q[j*W2 + r]
   T cs[W2];                          // c, s per pair of the current step
   T dd[W2];                          // updated diagonal per pair
   int pi[W2 / 2], pj[W2 / 2];
@@ -95,7 +97,48 @@ struct Smem {
   int vote[2];
 };
 
-// Gram G = Wc^T Wc for the W2 columns of the block pair (columns col[]).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem),
+               "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Stage chunk `ck` (rows ck*RC .. +RC of the W2 columns col[]) into buffer `dst`.
+// Aligned case (lda a multiple of the 16-byte vector): asynchronous 16-byte copies with
+// zero fill past the last row and for padding columns.  Otherwise plain loads.
+template <typename T, int W2>
+__device__ __forceinline__ void stage_chunk(const int *col, const T *__restrict__ Wsl, int rows,
+                                            int lda, bool aligned, int ck, T *dst) {
+  using C = Cfg<T, W2>;
+  const int r0 = ck * C::RC;
+  if (aligned) {
+    constexpr int VPC = C::RC / C::VN;                // vectors per column
+    for (int idx = threadIdx.x; idx < W2 * VPC; idx += NT) {
+      int c = idx / VPC, v = idx % VPC;
+      int gc = col[c];
+      int r = r0 + v * C::VN;
+      int valid = rows - r;
+      valid = valid < 0 ? 0 : (valid > C::VN ? C::VN : valid);
+      if (gc < 0) valid = 0;
+      const T *src = Wsl + (valid > 0 ? (int64_t)gc * lda + r : 0);
+      cp_async16(dst + c * C::LDR + v * C::VN, src, valid * (int)sizeof(T));
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < W2 * C::RC; idx += NT) {
+      int c = idx / C::RC, r = idx % C::RC;
+      int gc = col[c];
+      T v = T(0);
+      if (gc >= 0 && r0 + r < rows) v = ldcg(Wsl + (int64_t)gc * lda + r0 + r);
+      dst[c * C::LDR + r] = v;
+    }
+  }
+}
+
+// Gram G = Wc^T Wc for the W2 columns of the block pair (columns col[]), rows streamed
+// through an NS-stage cp.async pipeline (one barrier per chunk).
 template <typename T, int W2>
 __device__ void gram(Smem<T, W2> &s, const T *__restrict__ Wsl, int rows, int lda) {
   using C = Cfg<T, W2>;
@@ -104,21 +147,28 @@ __device__ void gram(Smem<T, W2> &s, const T *__restrict__ Wsl, int rows, int ld
   const int kg = tid / C::TILES;
   const int tile = tid % C::TILES;
   const int ti = tile / C::TD, tj = tile % C::TD;
+  const bool aligned = (lda % C::VN) == 0;
+  const int nck = (rows + C::RC - 1) / C::RC;
   T acc[4][4];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
 #pragma unroll
     for (int f = 0; f < 4; ++f) acc[e][f] = T(0);
-  T *ch = s.buf;
-  for (int r0 = 0; r0 < rows; r0 += C::RC) {
-    for (int idx = tid; idx < W2 * C::RC; idx += NT) {
-      int c = idx / C::RC, r = idx % C::RC;
-      int gc = s.col[c];
-      T v = T(0);
-      if (gc >= 0 && r0 + r < rows) v = ldcg(Wsl + (int64_t)gc * lda + r0 + r);
-      ch[c * C::LDR + r] = v;
-    }
+#pragma unroll
+  for (int c = 0; c < C::NS - 1; ++c) {
+    if (c < nck) stage_chunk<T, W2>(s.col, Wsl, rows, lda, aligned, c, s.buf + (c % C::NS) * C::CHUNK);
+    cp_async_commit();
+  }
+  for (int ck = 0; ck < nck; ++ck) {
+    cp_async_wait<C::NS - 2>();
     __syncthreads();
+    {
+      int nx = ck + C::NS - 1;
+      if (nx < nck) stage_chunk<T, W2>(s.col, Wsl, rows, lda, aligned, nx, s.buf + (nx % C::NS) * C::CHUNK);
+      cp_async_commit();
+    }
+    const T *ch = s.buf + (ck % C::NS) * C::CHUNK;
+#pragma unroll 2
     for (int r = kg * C::VN; r < C::RC; r += C::KG * C::VN) {
       T a[4][C::VN], b[4][C::VN];
 #pragma unroll
@@ -140,8 +190,9 @@ __device__ void gram(Smem<T, W2> &s, const T *__restrict__ Wsl, int rows, int ld
 #pragma unroll
           for (int f = 0; f < 4; ++f) acc[e][f] = fma(a[e][u], b[f][u], acc[e][f]);
     }
-    __syncthreads();
   }
+  cp_async_wait<0>();
+  __syncthreads();
   // reduce the K-groups in a fixed order
   T *gp = s.buf;
 #pragma unroll
@@ -159,10 +210,22 @@ __device__ void gram(Smem<T, W2> &s, const T *__restrict__ Wsl, int rows, int ld
   __syncthreads();
 }
 
-// One cyclic two-sided Jacobi sweep on G, accumulating the rotations in Q.
-// Returns (in s.any_rot) whether any pair was rotated.
+// Pair k of step `step` of one inner sweep.  full: the round-robin over all W2 columns
+// (W2-1 steps); cross: only pairs (i in block I, j in block J), B steps of B pairs.
+template <int W2>
+__device__ __forceinline__ void inner_pair(bool full, int step, int k, int &i, int &j) {
+  if (full) {
+    rr_pair(W2, step, k, i, j);
+  } else {
+    i = k;
+    j = W2 / 2 + (k + step) % (W2 / 2);
+  }
+}
+
+// One cyclic two-sided Jacobi sweep on G (all pairs when `full`, else only pairs across
+// the two blocks), accumulating the rotations in Q.  Sets s.any_rot.
 template <typename T, int W2>
-__device__ void inner_sweep(Smem<T, W2> &s, double tol) {
+__device__ void inner_sweep(Smem<T, W2> &s, double tol, bool full) {
   using C = Cfg<T, W2>;
   const int tid = threadIdx.x;
   constexpr int NP = W2 / 2;
@@ -170,7 +233,7 @@ __device__ void inner_sweep(Smem<T, W2> &s, double tol) {
   int need = 0;
   for (int idx = tid; idx < W2 * W2; idx += NT) {
     int i = idx / W2, j = idx % W2;
-    if (i < j) {
+    if (i < j && (full || (i < W2 / 2 && j >= W2 / 2))) {
       double a = (double)s.G[i * C::LDG + i], b = (double)s.G[j * C::LDG + j];
       double g = (double)s.G[i * C::LDG + j];
       if (isfinite(a) && isfinite(b) && fabs(g) > tol * sqrt(a * b)) need = 1;
@@ -180,10 +243,11 @@ __device__ void inner_sweep(Smem<T, W2> &s, double tol) {
   if (!__syncthreads_or(need)) return;
   for (int idx = tid; idx < W2 * W2; idx += NT) s.Q[idx] = (idx / W2 == idx % W2) ? T(1) : T(0);
   __syncthreads();
-  for (int step = 0; step < W2 - 1; ++step) {
+  const int nsteps = full ? W2 - 1 : W2 / 2;
+  for (int step = 0; step < nsteps; ++step) {
     if (tid < NP) {
       int i, j;
-      rr_pair(W2, step, tid, i, j);
+      inner_pair<W2>(full, step, tid, i, j);
       s.pi[tid] = i;
       s.pj[tid] = j;
       double a = (double)s.G[i * C::LDG + i];
@@ -242,42 +306,50 @@ __device__ void inner_sweep(Smem<T, W2> &s, double tol) {
       if (!s.rot[qq]) continue;
       int i = s.pi[qq], j = s.pj[qq];
       T c = s.cs[2 * qq], sn = s.cs[2 * qq + 1];
-      T x = s.Q[r * W2 + i], y = s.Q[r * W2 + j];
-      s.Q[r * W2 + i] = c * x - sn * y;
-      s.Q[r * W2 + j] = sn * x + c * y;
+      T x = s.Q[i * W2 + r], y = s.Q[j * W2 + r];
+      s.Q[i * W2 + r] = c * x - sn * y;
+      s.Q[j * W2 + r] = sn * x + c * y;
     }
     if (tid < NP && s.rot[tid]) atomicAdd((unsigned long long *)&s.nrot, 1ull);
     __syncthreads();
   }
 }
 
-// [Wsl(:, col)] <- [Wsl(:, col)] Q, streamed over row chunks.
+// [Wsl(:, col)] <- [Wsl(:, col)] Q, rows streamed through the cp.async pipeline; results
+// go straight from registers to global memory (each chunk's rows are read before they
+// are overwritten, and no other CTA touches these columns during the round).
 template <typename T, int W2>
 __device__ void apply_q(Smem<T, W2> &s, T *__restrict__ Wsl, int rows, int lda) {
   using C = Cfg<T, W2>;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  T *ch = s.buf;
-  for (int r0 = 0; r0 < rows; r0 += C::RC) {
-    for (int idx = tid; idx < W2 * C::RC; idx += NT) {
-      int c = idx / C::RC, r = idx % C::RC;
-      int gc = s.col[c];
-      T v = T(0);
-      if (gc >= 0 && r0 + r < rows) v = ldcg(Wsl + (int64_t)gc * lda + r0 + r);
-      ch[c * C::LDR + r] = v;
-    }
+  const bool aligned = (lda % C::VN) == 0;
+  const int nck = (rows + C::RC - 1) / C::RC;
+  const int j0 = warp * C::CPW;
+#pragma unroll
+  for (int c = 0; c < C::NS - 1; ++c) {
+    if (c < nck) stage_chunk<T, W2>(s.col, Wsl, rows, lda, aligned, c, s.buf + (c % C::NS) * C::CHUNK);
+    cp_async_commit();
+  }
+  for (int ck = 0; ck < nck; ++ck) {
+    cp_async_wait<C::NS - 2>();
     __syncthreads();
+    {
+      int nx = ck + C::NS - 1;
+      if (nx < nck) stage_chunk<T, W2>(s.col, Wsl, rows, lda, aligned, nx, s.buf + (nx % C::NS) * C::CHUNK);
+      cp_async_commit();
+    }
+    const T *ch = s.buf + (ck % C::NS) * C::CHUNK;
     T acc[C::RPT][C::CPW];
 #pragma unroll
     for (int q = 0; q < C::RPT; ++q)
 #pragma unroll
       for (int e = 0; e < C::CPW; ++e) acc[q][e] = T(0);
-    const int j0 = warp * C::CPW;
 #pragma unroll 4
     for (int c = 0; c < W2; ++c) {
       T qv[C::CPW];
 #pragma unroll
-      for (int e = 0; e < C::CPW; ++e) qv[e] = s.Q[c * W2 + j0 + e];
+      for (int e = 0; e < C::CPW; ++e) qv[e] = s.Q[(j0 + e) * W2 + c];
 #pragma unroll
       for (int q = 0; q < C::RPT; ++q) {
         T a = ch[c * C::LDR + lane + 32 * q];
@@ -285,6 +357,7 @@ __device__ void apply_q(Smem<T, W2> &s, T *__restrict__ Wsl, int rows, int lda) 
         for (int e = 0; e < C::CPW; ++e) acc[q][e] = fma(a, qv[e], acc[q][e]);
       }
     }
+    const int r0 = ck * C::RC;
 #pragma unroll
     for (int e = 0; e < C::CPW; ++e) {
       int gc = s.col[j0 + e];
@@ -295,8 +368,9 @@ __device__ void apply_q(Smem<T, W2> &s, T *__restrict__ Wsl, int rows, int lda) 
         if (r < rows) __stcg(Wsl + (int64_t)gc * lda + r, acc[q][e]);
       }
     }
-    __syncthreads();
   }
+  cp_async_wait<0>();
+  __syncthreads();
 }
 
 template <typename T, int W2>
@@ -345,7 +419,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiParams p) {
           }
           __syncthreads();
           gram<T, W2>(s, Wsl, rows, rows);
-          inner_sweep<T, W2>(s, tol);
+          inner_sweep<T, W2>(s, tol, round == 0);
           if (s.any_rot) {
             if (tid == 0) s.sweep_any = 1;
             apply_q<T, W2>(s, Wsl, rows, rows);
@@ -390,7 +464,7 @@ cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hi
   if (nb & 1) ++nb;
   if (nb < 2) nb = 2;
   int cl = 1;
-  int want = cluster_hint > 0 ? cluster_hint : 16;
+  int want = cluster_hint > 0 ? cluster_hint : (W2 >= 64 ? 4 : 16);
   while (cl * 2 <= want && cl * 2 <= nb / 2) cl *= 2;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -414,7 +488,7 @@ cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hi
   }
   // Limit the slices in flight so their working set (W and V) stays in L2.
   double slice_bytes = (double)sizeof(T) * ((double)p.rows * p.cols + (double)p.cols * p.cols);
-  int l2_clusters = (int)(64.0 * 1024 * 1024 / (slice_bytes > 1 ? slice_bytes : 1));
+  int l2_clusters = (int)(96.0 * 1024 * 1024 / (slice_bytes > 1 ? slice_bytes : 1));
   int nclusters = max_clusters;
   if (grid_hint > 0) nclusters = grid_hint;
   else if (l2_clusters < nclusters) nclusters = l2_clusters > 0 ? l2_clusters : 1;
@@ -577,10 +651,13 @@ __global__ void transpose_kernel(const T *__restrict__ A, int64_t m, int64_t p, 
 }  // namespace
 
 template <typename T>
-cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int cluster_hint, int grid_hint) {
-  if (p.cols <= 8) return launch_jacobi<T, 16>(p, st, cluster_hint, grid_hint);
-  if (p.cols <= 16) return launch_jacobi<T, 32>(p, st, cluster_hint, grid_hint);
-  return launch_jacobi<T, 32>(p, st, cluster_hint, grid_hint);
+cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, int cluster_hint,
+                       int grid_hint) {
+  int w = width_hint;
+  if (w != 16 && w != 32 && w != 64) w = p.cols <= 8 ? 16 : (p.cols <= 16 || p.cols < 256 ? 32 : 64);
+  if (w == 16) return launch_jacobi<T, 16>(p, st, cluster_hint, grid_hint);
+  if (w == 32) return launch_jacobi<T, 32>(p, st, cluster_hint, grid_hint);
+  return launch_jacobi<T, 64>(p, st, cluster_hint, grid_hint);
 }
 
 template <typename T>
@@ -619,7 +696,7 @@ cudaError_t transpose_slices(const T *A, int64_t m, int64_t p, int64_t nslices, 
 }
 
 #define INST(T)                                                                               \
-  template cudaError_t jacobi_run<T>(const JacobiParams &, cudaStream_t, int, int);           \
+  template cudaError_t jacobi_run<T>(const JacobiParams &, cudaStream_t, int, int, int);      \
   template cudaError_t jacobi_finalize<T>(const T *, int64_t, int, int, int, T *, int *,      \
                                           cudaStream_t);                                      \
   template cudaError_t emit_factors<T>(const T *, int64_t, const T *, int64_t, int, int, int, \
