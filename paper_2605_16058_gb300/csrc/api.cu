@@ -36,6 +36,8 @@ struct tsvdm_plan_s {
   double *scal = nullptr;
   double *splitk = nullptr;
   size_t splitk_elems = 0;
+  void *tc_ws = nullptr;
+  size_t tc_ws_bytes = 0;
   double tol = 0.0;
   int max_sweeps = 40;
   int width_hint = 0, cluster_hint = 0, grid_hint = 0;
@@ -129,22 +131,39 @@ tsvdm_status read_status(tsvdm_plan_s *p) {
   return TSVDM_OK;
 }
 
+// One mode-3 TTM in the plan's precision: tensor cores (tcgen05) for TF32 / BF16x3 when
+// the shape allows it, CUDA cores otherwise.
+template <typename T>
+cudaError_t ttm_any(tsvdm_plan_s *p, const T *X, int64_t P, const T *M, bool transB, T *Y,
+                    const double *scale, const double *beta, const T *Z, double *sumsq) {
+  const int64_t n = p->n3;
+  if constexpr (sizeof(T) == 4) {
+    if ((p->prec == TSVDM_P_TF32 || p->prec == TSVDM_P_BF16X3) && p->tc_ws &&
+        ttm_tc_supported(P, n, n, X, Y))
+      return ttm_tc((const float *)X, P, n, (const float *)M, n, transB, (int)p->prec, (float *)Y,
+                    p->tc_ws, p->tc_ws_bytes, sumsq, scale, beta, (const float *)Z, p->status,
+                    p->st);
+  }
+  return ttm_simt<T>(X, P, n, M, n, n, transB, Y, scale, beta, Z, sumsq, p->st);
+}
+
 template <typename T>
 tsvdm_status run_ttm(tsvdm_plan_s *p, const T *X, int64_t P, const T *M, bool inverse, T *Y,
                      double *sumsq) {
   const int64_t n = p->n3;
   stage_begin(p, TSVDM_STAGE_TTM);
   int nl = 1;
+  const bool tc = (p->prec == TSVDM_P_TF32 || p->prec == TSVDM_P_BF16X3);
   if (!inverse) {
-    CK(ttm_simt<T>(X, P, n, M, n, n, false, Y, nullptr, nullptr, nullptr, sumsq, p->st));
+    CK(ttm_any<T>(p, X, P, M, false, Y, nullptr, nullptr, nullptr, sumsq));
   } else if (p->ortho) {
     CK(inv_scale<T>(M, n, p->scal + SC_INVSCALE, p->st));
-    CK(ttm_simt<T>(X, P, n, M, n, n, true, Y, p->scal + SC_INVSCALE, nullptr, nullptr, sumsq,
-                   p->st));
+    CK(ttm_any<T>(p, X, P, M, true, Y, p->scal + SC_INVSCALE, nullptr, nullptr, sumsq));
     nl = 2;
   } else {
-    CK(ttm_simt<T>(X, P, n, M, n, n, false, Y, nullptr, nullptr, nullptr, sumsq, p->st));
+    CK(ttm_any<T>(p, X, P, M, false, Y, nullptr, nullptr, nullptr, sumsq));
   }
+  if (tc) nl += 1;   // the B-operand preparation kernel
   stage_end(p, TSVDM_STAGE_TTM, nl);
   return TSVDM_OK;
 }
@@ -327,8 +346,8 @@ tsvdm_status backward_impl(tsvdm_plan_s *p, const void *X, const void *M, int64_
   stage_end(p, TSVDM_STAGE_OTHER, 2);
   if (dX) {
     stage_begin(p, TSVDM_STAGE_TTM);
-    CK(ttm_simt<T>((const T *)p->Ahat, P, n, (const T *)M, n, n, true, (T *)dX,
-                   p->scal + SC_ALPHA, p->scal + SC_BETA, (const T *)X, nullptr, p->st));
+    CK(ttm_any<T>(p, (const T *)p->Ahat, P, (const T *)M, true, (T *)dX, p->scal + SC_ALPHA,
+                  p->scal + SC_BETA, (const T *)X, nullptr));
     stage_end(p, TSVDM_STAGE_TTM, 1);
   }
   if (dM) {
@@ -352,7 +371,7 @@ bool valid_plan(tsvdm_plan p) { return p != nullptr && p->Ahat != nullptr; }
 
 void free_plan(tsvdm_plan_s *p) {
   void *bufs[] = {p->Ahat, p->Wt, p->Vw, p->sig, p->keys, p->perm, p->sweeps, p->status,
-                  p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk};
+                  p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk, p->tc_ws};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < STG_COUNT; ++i)
@@ -391,7 +410,9 @@ tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype d
   if (n1 > (1 << 30) || n2 > (1 << 30) || n3 > (1 << 30)) return TSVDM_EINVAL;
   if (dtype != TSVDM_F32 && dtype != TSVDM_F64) return TSVDM_EINVAL;
   if (dtype == TSVDM_F64 && prec != TSVDM_P_FP64) return TSVDM_ENOTSUP;
-  if (dtype == TSVDM_F32 && prec != TSVDM_P_FP32) return TSVDM_ENOTSUP;
+  if (dtype == TSVDM_F32 && prec != TSVDM_P_FP32 && prec != TSVDM_P_TF32 &&
+      prec != TSVDM_P_BF16X3)
+    return TSVDM_ENOTSUP;
   tsvdm_plan_s *p = new (std::nothrow) tsvdm_plan_s();
   if (!p) return TSVDM_ENOMEM;
   p->n1 = n1;
@@ -433,6 +454,10 @@ tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype d
   AL(p->off_ws, sizeof(int64_t) * (n3 + 1));
   AL(p->scal, sizeof(double) * SC_COUNT);
   AL(p->splitk, sizeof(double) * p->splitk_elems);
+  if (prec == TSVDM_P_TF32 || prec == TSVDM_P_BF16X3) {
+    p->tc_ws_bytes = ttm_tc_workspace(n3, n3);
+    AL(p->tc_ws, p->tc_ws_bytes);
+  }
 #undef AL
   if (err == cudaSuccess) err = cudaMemset(p->status, 0, sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(p->scal, 0, sizeof(double) * SC_COUNT);

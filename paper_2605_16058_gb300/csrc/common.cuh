@@ -39,6 +39,16 @@ cudaError_t ttm_simt(const T *X, int64_t P, int64_t n, const T *M, int64_t ldm, 
                      bool transB, T *Y, const double *scale_ptr, const double *beta_ptr,
                      const T *Z, double *sumsq, cudaStream_t st);
 
+// Tensor-core (tcgen05) TTM in BF16x3 or TF32, FP32 accumulation; same semantics as
+// ttm_simt with ldm = n for the forward case (M is J x n, J <= 512).  Returns
+// cudaErrorNotSupported when the shape or alignment cannot use it.
+size_t ttm_tc_workspace(int64_t n, int64_t J);
+bool ttm_tc_supported(int64_t P, int64_t n, int64_t J, const void *X, const void *Y);
+cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t J, bool transB,
+                   int prec, float *Y, void *ws, size_t ws_bytes, double *sumsq,
+                   const double *scale_ptr, const double *beta_ptr, const float *Z, int *status,
+                   cudaStream_t st);
+
 // Transposed copy of each m x p slice (rows x cols) into p x m.
 template <typename T>
 cudaError_t transpose_slices(const T *A, int64_t m, int64_t p, int64_t nslices, T *B,

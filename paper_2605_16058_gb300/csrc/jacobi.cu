@@ -486,12 +486,9 @@ cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hi
     if (cl == 1) return e == cudaSuccess ? cudaErrorInvalidConfiguration : e;
     cl /= 2;
   }
-  // Limit the slices in flight so their working set (W and V) stays in L2.
-  double slice_bytes = (double)sizeof(T) * ((double)p.rows * p.cols + (double)p.cols * p.cols);
-  int l2_clusters = (int)(96.0 * 1024 * 1024 / (slice_bytes > 1 ? slice_bytes : 1));
+  // All co-resident clusters (measured faster than keeping the slices in flight within L2).
   int nclusters = max_clusters;
   if (grid_hint > 0) nclusters = grid_hint;
-  else if (l2_clusters < nclusters) nclusters = l2_clusters > 0 ? l2_clusters : 1;
   if (nclusters > p.nslices) nclusters = p.nslices;
   if (nclusters < 1) nclusters = 1;
   cfg.gridDim = dim3(nclusters * cl);

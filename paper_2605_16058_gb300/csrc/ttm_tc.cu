@@ -1,0 +1,466 @@
+// Mode-3 TTM on the 5th-generation tensor cores (tcgen05 + TMEM), fed by TMA.
+//
+// Y (P x J) = scale * X (P x n) B (n x J) [+ beta Z], the last-mode TTM as one GEMM
+// (Sec. 3.1), B(t, i) = M(i, t) (forward) or M(t, i) (transposed).  One CTA owns a tile
+// of 128 rows of X and ALL J <= 512 outputs (the accumulator lives in TMEM, 128 lanes x
+// up to 512 FP32 columns), so X is read from HBM exactly once.
+//
+// Precision modes (FP32 accumulation in TMEM in both):
+//   BF16x3  x = x_hi + x_lo with x_hi = bf16(x), x_lo = bf16(x - x_hi) (same split for B);
+//           D += A_hi B_hi + A_hi B_lo + A_lo B_hi  (three kind::f16 MMAs per k-step)
+//   TF32    D += A B with both operands rounded to TF32 (one kind::tf32 MMA per k-step)
+//
+// Warp roles (256 threads):
+//   warp 0      TMA producer: raw FP32 X tile (128 rows x 32 t, no swizzle) and the
+//               pre-converted K-major B tiles (swizzled) of each stage;
+//   warp 1      TMEM allocation; one thread issues the MMAs and commits them;
+//   warps 4..7  converters (thread = row): FP32 X -> K-major swizzled operand tiles,
+//               then the epilogue (tcgen05.ld of its own TMEM lane -> scale -> store).
+// Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT in the status
+// word and runs to completion (TMEM is always released).  Nothing traps.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace tsvdm {
+namespace {
+
+constexpr int TBM = 128;
+constexpr int TBK = 32;
+constexpr int STAGES = 2;
+constexpr int TC_THREADS = 256;
+constexpr unsigned SPIN_LIMIT = 1u << 26;
+
+struct TcParams {
+  int64_t P, n, J;
+  int npad;          // J rounded up to 16 (J <= 256) or to 128 (J <= 512)
+  int box_rows;      // rows of one B tensor-map box (divides npad, <= 256)
+  int kt_count;      // ceil(n / TBK)
+  int prec;          // TSVDM_P_BF16X3 or TSVDM_P_TF32
+  float *Y;
+  const float *Z;
+  const double *scale_ptr, *beta_ptr;
+  double *sumsq;
+  int *status;
+  uint32_t tmem_cols;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait for the phase with parity `par`; returns false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t par) {
+  uint32_t a = smem_u32(bar);
+  for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(par)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, swizzled; sbo = byte stride between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t sbo, uint32_t layout) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_u32(p) >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused, K-major)
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)layout << 61;                     // 2 = 128B swizzle, 4 = 64B swizzle
+  return d;
+}
+
+// Instruction descriptor: D FP32, A/B format `fmt` (1 = BF16 for kind::f16, 2 = TF32 for
+// kind::tf32), both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc(uint32_t fmt, uint32_t n) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// Shared memory of one CTA.  Offsets are multiples of 1024 bytes (swizzle atoms).
+struct TcLayout {
+  uint32_t raw, a, b, stage, total;
+  uint32_t a_bytes, b_bytes;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int npad, int prec) {
+  TcLayout L;
+  const uint32_t raw = TBK * TBM * 4;                       // 16 KB
+  const uint32_t a = (prec == TSVDM_P_BF16X3) ? 2u * TBM * 64 : TBM * 128u;   // 16 KB
+  const uint32_t b = (prec == TSVDM_P_BF16X3) ? 2u * npad * 64 : npad * 128u;
+  L.a_bytes = a;
+  L.b_bytes = b;
+  L.raw = 0;
+  L.a = raw;
+  L.b = raw + a;
+  uint32_t st = raw + a + b;
+  st = (st + 1023) & ~1023u;
+  L.stage = st;
+  L.total = STAGES * st + 1024;                            // + barriers / TMEM address
+  return L;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    ttm_tc_kernel(const __grid_constant__ CUtensorMap mapX,
+                  const __grid_constant__ CUtensorMap mapB, TcParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // align the dynamic shared memory base to 1024 bytes
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const TcLayout L = tc_layout(p.npad, p.prec);
+  uint64_t *full = (uint64_t *)(smem + STAGES * L.stage);
+  uint64_t *conv = full + STAGES;
+  uint64_t *empty = conv + STAGES;
+  uint64_t *done = empty + STAGES;
+  uint32_t *tmem_slot = (uint32_t *)(done + 1);
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * TBM;
+  const bool bf = p.prec == TSVDM_P_BF16X3;
+  const int nk = p.kt_count;
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    const uint32_t bytes = TBK * TBM * 4 + L.b_bytes;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES, u = kt / STAGES;
+      if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) { s_fail = 1; break; }
+      unsigned char *st = smem + s * L.stage;
+      mbar_expect_tx(&full[s], bytes);
+      tma_load_2d(st + L.raw, &mapX, &full[s], (int)m0, kt * TBK);
+      // B: [ops][npad rows][32 K]; box rows <= 256
+      const int ops = bf ? 2 : 1;
+      const uint32_t row_bytes = bf ? 64 : 128;
+      for (int o = 0; o < ops; ++o)
+        for (int r0 = 0; r0 < p.npad; r0 += p.box_rows)
+          tma_load_2d(st + L.b + (uint32_t)o * p.npad * row_bytes + (uint32_t)r0 * row_bytes,
+                      &mapB, &full[s], kt * TBK, o * p.npad + r0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t fmt = bf ? 1u : 2u;
+    const uint32_t sbo = bf ? 512u : 1024u;
+    const uint32_t lay = bf ? 4u : 2u;
+    const uint32_t row_bytes = bf ? 64u : 128u;
+    const int ksub = bf ? TBK / 16 : TBK / 8;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES, u = kt / STAGES;
+      if (!mbar_wait(&conv[s], u & 1)) { s_fail = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned char *st = smem + s * L.stage;
+      for (int kk = 0; kk < ksub; ++kk) {
+        const uint32_t koff = kk * 32;                      // 32 bytes per k-step
+        for (int n0 = 0; n0 < p.npad; n0 += 256) {
+          const uint32_t nn = (p.npad - n0) < 256 ? (uint32_t)(p.npad - n0) : 256u;
+          const uint32_t idesc = instr_desc(fmt, nn);
+          const uint32_t d = tmem + (uint32_t)n0;
+          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+          if (bf) {
+            uint64_t ahi = smem_desc(st + L.a + koff, sbo, lay);
+            uint64_t alo = smem_desc(st + L.a + TBM * 64 + koff, sbo, lay);
+            uint64_t bhi = smem_desc(st + L.b + n0 * row_bytes + koff, sbo, lay);
+            uint64_t blo = smem_desc(st + L.b + (uint32_t)p.npad * row_bytes + n0 * row_bytes + koff,
+                                     sbo, lay);
+            mma_f16(d, ahi, bhi, idesc, acc);
+            mma_f16(d, ahi, blo, idesc, 1u);
+            mma_f16(d, alo, bhi, idesc, 1u);
+          } else {
+            uint64_t a = smem_desc(st + L.a + koff, sbo, lay);
+            uint64_t b = smem_desc(st + L.b + n0 * row_bytes + koff, sbo, lay);
+            mma_tf32(d, a, b, idesc, acc);
+          }
+        }
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  } else if (warp >= 4) {
+    // ---------------- converters, then epilogue
+    const int row = tid - 128;
+    double ss = 0.0;
+    const bool do_ss = p.sumsq != nullptr;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES, u = kt / STAGES;
+      if (!mbar_wait(&full[s], u & 1)) { s_fail = 1; break; }
+      unsigned char *st = smem + s * L.stage;
+      const float *raw = (const float *)(st + L.raw);
+      float x[TBK];
+#pragma unroll
+      for (int k = 0; k < TBK; ++k) x[k] = raw[k * TBM + row];
+      if (do_ss) {
+#pragma unroll
+        for (int k = 0; k < TBK; ++k) ss += (double)x[k] * (double)x[k];
+      }
+      if (bf) {
+        unsigned char *ahi = st + L.a, *alo = st + L.a + TBM * 64;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t h[4], l[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float x0 = x[c * 8 + 2 * q], x1 = x[c * 8 + 2 * q + 1];
+            __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+            __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          }
+          const uint32_t off = (uint32_t)row * 64 + (((uint32_t)c ^ (((uint32_t)row >> 1) & 3)) << 4);
+          *(uint4 *)(ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+          *(uint4 *)(alo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+      } else {
+        unsigned char *a = st + L.a;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          uint32_t v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v[q]) : "f"(x[c * 4 + q]));
+          const uint32_t off = (uint32_t)row * 128 + (((uint32_t)c ^ ((uint32_t)row & 7)) << 4);
+          *(uint4 *)(a + off) = make_uint4(v[0], v[1], v[2], v[3]);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&conv[s]);
+    }
+    if (do_ss) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) atomicAdd(p.sumsq, ss);
+    }
+    // epilogue
+    const bool ok = mbar_wait(done, 0);
+    if (!ok) s_fail = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const float scale = p.scale_ptr ? (float)(*p.scale_ptr) : 1.f;
+    const float beta = p.beta_ptr ? (float)(*p.beta_ptr) : 0.f;
+    const int64_t grow = m0 + row;
+    const uint32_t lane_base = (uint32_t)(32 * (warp - 4)) << 16;
+    for (int j0 = 0; j0 < p.npad; j0 += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + lane_base + (uint32_t)j0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (ok && grow < p.P) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int64_t col = j0 + e;
+          if (col < p.J) {
+            float y = scale * __uint_as_float(v[e]);
+            if (p.Z) y = fmaf(beta, p.Z[grow + p.P * col], y);
+            p.Y[grow + p.P * col] = y;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+  if (tid == 0 && s_fail) atomicOr(p.status, ST_TIMEOUT);
+}
+
+// Bk: operand B of the TTM in K-major layout, [ops][npad][kpad] (K contiguous), zero
+// padded.  BF16x3: ops = 2 (hi, lo) bf16; TF32: ops = 1, FP32 rounded to TF32.
+__global__ void prep_b_kernel(const float *__restrict__ M, int64_t n, int64_t J, bool transB,
+                              int npad, int kpad, int prec, void *Bk) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)npad * kpad) return;
+  const int64_t i = idx / kpad, t = idx % kpad;     // output column i, contraction index t
+  float b = 0.f;
+  if (i < J && t < n) b = transB ? M[t + n * i] : M[i + J * t];
+  if (prec == TSVDM_P_BF16X3) {
+    __nv_bfloat16 h = __float2bfloat16_rn(b);
+    __nv_bfloat16 l = __float2bfloat16_rn(b - __bfloat162float(h));
+    __nv_bfloat16 *o = (__nv_bfloat16 *)Bk;
+    o[i * kpad + t] = h;
+    o[(int64_t)npad * kpad + i * kpad + t] = l;
+  } else {
+    uint32_t v;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v) : "f"(b));
+    ((uint32_t *)Bk)[i * kpad + t] = v;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+}  // namespace
+
+static int tc_npad(int64_t J) { return J <= 256 ? (int)((J + 15) / 16 * 16) : (int)((J + 127) / 128 * 128); }
+
+size_t ttm_tc_workspace(int64_t n, int64_t J) {
+  int64_t npad = tc_npad(J), kpad = (n + TBK - 1) / TBK * TBK;
+  return (size_t)2 * npad * kpad * 2 + 4096;           // bf16 hi+lo (tf32 needs the same)
+}
+
+bool ttm_tc_supported(int64_t P, int64_t n, int64_t J, const void *X, const void *Y) {
+  if (J < 1 || J > 512 || n < 1 || P < 1) return false;
+  if ((P % 4) != 0) return false;                      // 16-byte row stride of the X view
+  if (((uintptr_t)X & 15) != 0 || ((uintptr_t)Y & 3) != 0) return false;
+  if (P > (int64_t)0x7fffffff) return false;
+  return get_encode() != nullptr;
+}
+
+cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t J, bool transB,
+                   int prec, float *Y, void *ws, size_t ws_bytes, double *sumsq,
+                   const double *scale_ptr, const double *beta_ptr, const float *Z, int *status,
+                   cudaStream_t st) {
+  if (!ttm_tc_supported(P, n, J, X, Y)) return cudaErrorNotSupported;
+  if (prec != TSVDM_P_BF16X3 && prec != TSVDM_P_TF32) return cudaErrorInvalidValue;
+  const int npad = tc_npad(J);
+  const int kpad = (int)((n + TBK - 1) / TBK * TBK);
+  const int box_rows = npad <= 256 ? npad : 128;
+  if (ws_bytes < ttm_tc_workspace(n, J)) return cudaErrorInvalidValue;
+  void *Bk = (void *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  {
+    int64_t cnt = (int64_t)npad * kpad;
+    prep_b_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(M, n, J, transB, npad, kpad, prec,
+                                                                  Bk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  auto enc = get_encode();
+  CUtensorMap mapX, mapB;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)P * 4};
+    cuuint32_t box[2] = {TBM, TBK};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&mapX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)X, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const bool bf = prec == TSVDM_P_BF16X3;
+    const int ops = bf ? 2 : 1;
+    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)npad * ops};
+    cuuint64_t strides[1] = {(cuuint64_t)kpad * (bf ? 2 : 4)};
+    cuuint32_t box[2] = {TBK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&mapB, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Bk,
+            dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            bf ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  TcParams p;
+  p.P = P;
+  p.n = n;
+  p.J = J;
+  p.npad = npad;
+  p.box_rows = box_rows;
+  p.kt_count = kpad / TBK;
+  p.prec = prec;
+  p.Y = Y;
+  p.Z = Z;
+  p.scale_ptr = scale_ptr;
+  p.beta_ptr = beta_ptr;
+  p.sumsq = sumsq;
+  p.status = status;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)npad) cols <<= 1;
+  p.tmem_cols = cols;
+  const TcLayout L = tc_layout(npad, prec);
+  const size_t smem = L.total + 1024;
+  cudaError_t e = cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((P + TBM - 1) / TBM);
+  ttm_tc_kernel<<<grid, TC_THREADS, smem, st>>>(mapX, mapB, p);
+  return cudaGetLastError();
+}
+
+}  // namespace tsvdm
