@@ -99,9 +99,12 @@ tsvdm_status tsvdm_plan_set_jacobi(tsvdm_plan plan, double tol, int max_sweeps);
 /* Launch shape of the batched Jacobi kernel (for tuning; 0 = automatic).  block_width:
  * columns of a block pair (16, 32 or 64); cluster_size: CTAs that share one slice
  * (1..16, powers of two, capped by the block pairs of a round and by the device);
- * clusters: clusters launched (slices in flight).  EINVAL for other values. */
+ * clusters: clusters launched (slices in flight); stages: row-chunk pipeline depth
+ * (2 or 3); ordering: 1 = columns re-ordered by decreasing norm at every sweep
+ * (de Rijk), 2 = natural column order; inner_sweeps: Gram sweeps per block pair
+ * (1..8).  EINVAL for other values. */
 tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster_size,
-                                   int clusters);
+                                   int clusters, int stages, int ordering, int inner_sweeps);
 
 /* Y = X x_3 M (inverse = 0) or Y = X x_3 M^{-1} (inverse = 1), Sec. 2.1.  For
  * inverse = 1 on an orthogonal plan, M is the forward matrix and M^T / c^2 is applied;

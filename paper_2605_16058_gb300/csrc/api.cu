@@ -33,6 +33,8 @@ struct tsvdm_plan_s {
   int *ranks_ws = nullptr;
   int64_t *off_ws = nullptr;
   long long *rots = nullptr;
+  float *norm2 = nullptr;
+  int sort_cols = 1;
   double *scal = nullptr;
   double *splitk = nullptr;
   size_t splitk_elems = 0;
@@ -40,7 +42,7 @@ struct tsvdm_plan_s {
   size_t tc_ws_bytes = 0;
   double tol = 0.0;
   int max_sweeps = 40;
-  int width_hint = 0, cluster_hint = 0, grid_hint = 0;
+  int width_hint = 0, cluster_hint = 0, grid_hint = 0, stages_hint = 0, inner_sweeps = 1;
   int tol_valid = 0;
   int64_t tol_total = 0;
   void *stage[STG_COUNT] = {};
@@ -196,8 +198,10 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   jp.status = p->status;
   jp.sweeps = p->sweeps;
   jp.rots = p->rots;
+  jp.norm2 = p->sort_cols ? p->norm2 : nullptr;
+  jp.inner_sweeps = p->inner_sweeps;
   stage_begin(p, TSVDM_STAGE_JACOBI);
-  CK(jacobi_run<T>(jp, p->st, p->width_hint, p->cluster_hint, p->grid_hint));
+  CK(jacobi_run<T>(jp, p->st, p->width_hint, p->cluster_hint, p->grid_hint, p->stages_hint));
   stage_end(p, TSVDM_STAGE_JACOBI, 1);
   stage_begin(p, TSVDM_STAGE_FINALIZE);
   CK(jacobi_finalize<T>((const T *)work_matrix(p), jp.sA, jp.rows, jp.cols, jp.nslices,
@@ -371,7 +375,8 @@ bool valid_plan(tsvdm_plan p) { return p != nullptr && p->Ahat != nullptr; }
 
 void free_plan(tsvdm_plan_s *p) {
   void *bufs[] = {p->Ahat, p->Wt, p->Vw, p->sig, p->keys, p->perm, p->sweeps, p->status,
-                  p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk, p->tc_ws};
+                  p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk, p->tc_ws,
+                  p->norm2};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < STG_COUNT; ++i)
@@ -448,6 +453,7 @@ tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype d
   AL(p->keys, 2 * sizeof(unsigned long long) * ns);
   AL(p->sweeps, sizeof(int) * n3);
   AL(p->rots, sizeof(long long) * n3);
+  AL(p->norm2, sizeof(float) * ns);
   AL(p->status, sizeof(int));
   AL(p->queue, sizeof(int));
   AL(p->ranks_ws, sizeof(int) * n3);
@@ -485,12 +491,18 @@ tsvdm_status tsvdm_plan_set_jacobi(tsvdm_plan plan, double tol, int max_sweeps) 
 }
 
 tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster_size,
-                                   int clusters) {
+                                   int clusters, int stages, int ordering, int inner_sweeps) {
   if (!valid_plan(plan)) return TSVDM_EINVAL;
   if (block_width != 0 && block_width != 16 && block_width != 32 && block_width != 64)
     return TSVDM_EINVAL;
   if (cluster_size < 0 || cluster_size > 16 || clusters < 0) return TSVDM_EINVAL;
+  if (stages != 0 && stages != 2 && stages != 3) return TSVDM_EINVAL;
+  if (ordering < 0 || ordering > 2) return TSVDM_EINVAL;
+  if (inner_sweeps < 0 || inner_sweeps > 8) return TSVDM_EINVAL;
+  plan->inner_sweeps = inner_sweeps > 0 ? inner_sweeps : 1;
   plan->width_hint = block_width;
+  plan->stages_hint = stages;
+  plan->sort_cols = ordering == 2 ? 0 : 1;
   plan->cluster_hint = cluster_size;
   plan->grid_hint = clusters;
   return TSVDM_OK;

@@ -66,11 +66,13 @@ struct JacobiParams {
   int *status;         // status word
   int *sweeps;         // [nslices] sweeps executed (-1 = cap reached)
   long long *rots;     // [nslices] rotations applied
+  float *norm2;        // [nslices * cols] squared column norms (nullptr: natural order)
+  int inner_sweeps;    // Gram sweeps per block pair (>= 1)
 };
 
 template <typename T>
 cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, int cluster_hint,
-                       int grid_hint);
+                       int grid_hint, int stages);
 
 // sigma (sorted descending) and the column permutation of each slice.
 template <typename T>

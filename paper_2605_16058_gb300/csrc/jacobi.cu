@@ -39,11 +39,11 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 
-template <typename T, int W2>
+template <typename T, int W2, int NS_ = 3>
 struct Cfg {
   static constexpr int B = W2 / 2;                    // block width
   static constexpr int RC = 4096 / W2;                // rows per pipelined chunk
-  static constexpr int NS = 3;                        // pipeline stages
+  static constexpr int NS = NS_;                      // pipeline stages
   static constexpr int VN = Vec16<T>::N;
   static constexpr int LDR = RC + VN;                 // chunk column stride (elements)
   static constexpr int TD = W2 / 4;                   // Gram tiles per dimension
@@ -79,10 +79,12 @@ __device__ __forceinline__ void rr_pair(int n, int round, int q, int &a, int &b)
 template <typename T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
-template <typename T, int W2>
+constexpr int MAXSORT = 1024;        // slices with more columns keep the natural order
+
+template <typename T, int W2, int NS>
 struct Smem {
-  T buf[Cfg<T, W2>::BUF];            // streamed chunk / Gram partials
-  T G[W2 * Cfg<T, W2>::LDG];         // Gram matrix
+  T buf[Cfg<T, W2, NS>::BUF];            // streamed chunk / Gram partials
+  T G[W2 * Cfg<T, W2, NS>::LDG];         // Gram matrix
   T Q[W2 * W2];                      // accumulated rotation, Q(r, j) at Q[j*W2 + r]
   T cs[W2];                          // c, s per pair of the current step
   T dd[W2];                          // updated diagonal per pair
@@ -90,11 +92,13 @@ struct Smem {
   int rot[W2 / 2];
   int col[W2];                       // global column of local column c (-1 = padding)
   int any_rot;                       // this block pair rotated
+  int step_rot;                      // the last inner sweep rotated
   int sweep_any;                     // this CTA rotated in this sweep
   int nonfinite;
   long long nrot;
   int slice[2];
   int vote[2];
+  int ord[MAXSORT];                  // column order of the current sweep
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
@@ -109,10 +113,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Stage chunk `ck` (rows ck*RC .. +RC of the W2 columns col[]) into buffer `dst`.
 // Aligned case (lda a multiple of the 16-byte vector): asynchronous 16-byte copies with
 // zero fill past the last row and for padding columns.  Otherwise plain loads.
-template <typename T, int W2>
+template <typename T, int W2, int NS>
 __device__ __forceinline__ void stage_chunk(const int *col, const T *__restrict__ Wsl, int rows,
                                             int lda, bool aligned, int ck, T *dst) {
-  using C = Cfg<T, W2>;
+  using C = Cfg<T, W2, NS>;
   const int r0 = ck * C::RC;
   if (aligned) {
     constexpr int VPC = C::RC / C::VN;                // vectors per column
@@ -139,9 +143,9 @@ __device__ __forceinline__ void stage_chunk(const int *col, const T *__restrict_
 
 // Gram G = Wc^T Wc for the W2 columns of the block pair (columns col[]), rows streamed
 // through an NS-stage cp.async pipeline (one barrier per chunk).
-template <typename T, int W2>
-__device__ void gram(Smem<T, W2> &s, const T *__restrict__ Wsl, int rows, int lda) {
-  using C = Cfg<T, W2>;
+template <typename T, int W2, int NS>
+__device__ void gram(Smem<T, W2, NS> &s, const T *__restrict__ Wsl, int rows, int lda) {
+  using C = Cfg<T, W2, NS>;
   using V = typename Vec16<T>::type;
   const int tid = threadIdx.x;
   const int kg = tid / C::TILES;
@@ -156,7 +160,7 @@ __device__ void gram(Smem<T, W2> &s, const T *__restrict__ Wsl, int rows, int ld
     for (int f = 0; f < 4; ++f) acc[e][f] = T(0);
 #pragma unroll
   for (int c = 0; c < C::NS - 1; ++c) {
-    if (c < nck) stage_chunk<T, W2>(s.col, Wsl, rows, lda, aligned, c, s.buf + (c % C::NS) * C::CHUNK);
+    if (c < nck) stage_chunk<T, W2, NS>(s.col, Wsl, rows, lda, aligned, c, s.buf + (c % C::NS) * C::CHUNK);
     cp_async_commit();
   }
   for (int ck = 0; ck < nck; ++ck) {
@@ -164,7 +168,7 @@ __device__ void gram(Smem<T, W2> &s, const T *__restrict__ Wsl, int rows, int ld
     __syncthreads();
     {
       int nx = ck + C::NS - 1;
-      if (nx < nck) stage_chunk<T, W2>(s.col, Wsl, rows, lda, aligned, nx, s.buf + (nx % C::NS) * C::CHUNK);
+      if (nx < nck) stage_chunk<T, W2, NS>(s.col, Wsl, rows, lda, aligned, nx, s.buf + (nx % C::NS) * C::CHUNK);
       cp_async_commit();
     }
     const T *ch = s.buf + (ck % C::NS) * C::CHUNK;
@@ -224,24 +228,32 @@ __device__ __forceinline__ void inner_pair(bool full, int step, int k, int &i, i
 
 // One cyclic two-sided Jacobi sweep on G (all pairs when `full`, else only pairs across
 // the two blocks), accumulating the rotations in Q.  Sets s.any_rot.
-template <typename T, int W2>
-__device__ void inner_sweep(Smem<T, W2> &s, double tol, bool full) {
-  using C = Cfg<T, W2>;
+template <typename T, int W2, int NS>
+__device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool first) {
+  using C = Cfg<T, W2, NS>;
   const int tid = threadIdx.x;
   constexpr int NP = W2 / 2;
   // fresh-Gram convergence test: does any pair exceed the threshold?
+  // |g| > tol sqrt(a b)  <=>  g^2 > tol^2 a b   (a, b >= 0; FP64, no square root)
+  const double tol2 = tol * tol;
   int need = 0;
   for (int idx = tid; idx < W2 * W2; idx += NT) {
     int i = idx / W2, j = idx % W2;
     if (i < j && (full || (i < W2 / 2 && j >= W2 / 2))) {
       double a = (double)s.G[i * C::LDG + i], b = (double)s.G[j * C::LDG + j];
       double g = (double)s.G[i * C::LDG + j];
-      if (isfinite(a) && isfinite(b) && fabs(g) > tol * sqrt(a * b)) need = 1;
+      if (isfinite(a) && isfinite(b) && g * g > tol2 * (a * b)) need = 1;
     }
   }
-  if (tid == 0) s.any_rot = 0;
+  __syncthreads();                   // every thread has read step_rot of the previous call
+  if (tid == 0) {
+    s.step_rot = 0;
+    if (first) s.any_rot = 0;
+  }
   if (!__syncthreads_or(need)) return;
-  for (int idx = tid; idx < W2 * W2; idx += NT) s.Q[idx] = (idx / W2 == idx % W2) ? T(1) : T(0);
+  if (first) {
+    for (int idx = tid; idx < W2 * W2; idx += NT) s.Q[idx] = (idx / W2 == idx % W2) ? T(1) : T(0);
+  }
   __syncthreads();
   const int nsteps = full ? W2 - 1 : W2 / 2;
   for (int step = 0; step < nsteps; ++step) {
@@ -256,16 +268,20 @@ __device__ void inner_sweep(Smem<T, W2> &s, double tol, bool full) {
       int rot = 0;
       if (!(isfinite(a) && isfinite(b))) {
         s.nonfinite = 1;
-      } else if (fabs(g) > tol * sqrt(a * b)) {
-        double zeta = (b - a) / (2.0 * g);
-        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + t * t);
+      } else if (g * g > tol2 * (a * b)) {
+        // zeta = (b - a) / (2 g);  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
+        //   = sign(zeta) |2g| / (|b - a| + sqrt((b - a)^2 + 4 g^2))   (one sqrt, one divide)
+        const double h = b - a, g2 = 2.0 * g;
+        const double sgn = ((h >= 0.0) == (g2 >= 0.0)) ? 1.0 : -1.0;
+        const double t = sgn * fabs(g2) / (fabs(h) + sqrt(h * h + g2 * g2));
+        const double c = rsqrt(1.0 + t * t);
         s.cs[2 * tid] = (T)c;
         s.cs[2 * tid + 1] = (T)(c * t);
         s.dd[2 * tid] = (T)(a - t * g);
         s.dd[2 * tid + 1] = (T)(b + t * g);
         rot = 1;
         s.any_rot = 1;
+        s.step_rot = 1;
       }
       if (!rot) {
         s.cs[2 * tid] = T(1);
@@ -318,9 +334,9 @@ __device__ void inner_sweep(Smem<T, W2> &s, double tol, bool full) {
 // [Wsl(:, col)] <- [Wsl(:, col)] Q, rows streamed through the cp.async pipeline; results
 // go straight from registers to global memory (each chunk's rows are read before they
 // are overwritten, and no other CTA touches these columns during the round).
-template <typename T, int W2>
-__device__ void apply_q(Smem<T, W2> &s, T *__restrict__ Wsl, int rows, int lda) {
-  using C = Cfg<T, W2>;
+template <typename T, int W2, int NS>
+__device__ void apply_q(Smem<T, W2, NS> &s, T *__restrict__ Wsl, int rows, int lda) {
+  using C = Cfg<T, W2, NS>;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const bool aligned = (lda % C::VN) == 0;
@@ -328,7 +344,7 @@ __device__ void apply_q(Smem<T, W2> &s, T *__restrict__ Wsl, int rows, int lda) 
   const int j0 = warp * C::CPW;
 #pragma unroll
   for (int c = 0; c < C::NS - 1; ++c) {
-    if (c < nck) stage_chunk<T, W2>(s.col, Wsl, rows, lda, aligned, c, s.buf + (c % C::NS) * C::CHUNK);
+    if (c < nck) stage_chunk<T, W2, NS>(s.col, Wsl, rows, lda, aligned, c, s.buf + (c % C::NS) * C::CHUNK);
     cp_async_commit();
   }
   for (int ck = 0; ck < nck; ++ck) {
@@ -336,7 +352,7 @@ __device__ void apply_q(Smem<T, W2> &s, T *__restrict__ Wsl, int rows, int lda) 
     __syncthreads();
     {
       int nx = ck + C::NS - 1;
-      if (nx < nck) stage_chunk<T, W2>(s.col, Wsl, rows, lda, aligned, nx, s.buf + (nx % C::NS) * C::CHUNK);
+      if (nx < nck) stage_chunk<T, W2, NS>(s.col, Wsl, rows, lda, aligned, nx, s.buf + (nx % C::NS) * C::CHUNK);
       cp_async_commit();
     }
     const T *ch = s.buf + (ck % C::NS) * C::CHUNK;
@@ -373,11 +389,11 @@ __device__ void apply_q(Smem<T, W2> &s, T *__restrict__ Wsl, int rows, int lda) 
   __syncthreads();
 }
 
-template <typename T, int W2>
-__global__ void __launch_bounds__(NT) jacobi_kernel(JacobiParams p) {
-  using C = Cfg<T, W2>;
+template <typename T, int W2, int NS>
+__global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParams p) {
+  using C = Cfg<T, W2, NS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T, W2> &s = *reinterpret_cast<Smem<T, W2> *>(smem_raw);
+  Smem<T, W2, NS> &s = *reinterpret_cast<Smem<T, W2, NS> *>(smem_raw);
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int csize = (int)cluster.num_blocks();
@@ -406,24 +422,61 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiParams p) {
     }
     cluster.sync();
 
+    const bool sorted = p.norm2 != nullptr && cols <= MAXSORT;
     int converged = 0, sweep = 0;
     for (sweep = 1; sweep <= p.max_sweeps; ++sweep) {
       if (tid == 0) s.sweep_any = 0;
+      if (sorted) {
+        // de Rijk ordering: columns by decreasing norm (ties: lower index first), from the
+        // squared norms the previous sweep left in norm2; the first sweep keeps 0..cols-1.
+        int p2 = 1;
+        while (p2 < cols) p2 <<= 1;
+        float *key = reinterpret_cast<float *>(s.buf);
+        const float *nrm = p.norm2 + (int64_t)slice * cols;
+        for (int c = tid; c < p2; c += NT) {
+          key[c] = c < cols ? (sweep == 1 ? -(float)c : __ldcg(nrm + c)) : -INFINITY;
+          s.ord[c] = c;
+        }
+        __syncthreads();
+        for (int k = 2; k <= p2; k <<= 1) {
+          for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = tid; t < p2; t += NT) {
+              int u = t ^ j;
+              if (u > t) {
+                float kt = key[t], ku = key[u];
+                int it = s.ord[t], iu = s.ord[u];
+                bool t_first = (kt > ku) || (kt == ku && it < iu);
+                if (((t & k) == 0) ? !t_first : t_first) {
+                  key[t] = ku; key[u] = kt;
+                  s.ord[t] = iu; s.ord[u] = it;
+                }
+              }
+            }
+            __syncthreads();
+          }
+        }
+      }
       for (int round = 0; round < nb - 1; ++round) {
         for (int q = crank; q < nb / 2; q += csize) {
           int bi, bj;
           rr_pair(nb, round, q, bi, bj);
           if (tid < W2) {
-            int gc = (tid < C::B) ? bi * C::B + tid : bj * C::B + (tid - C::B);
-            s.col[tid] = gc < cols ? gc : -1;
+            int lc = (tid < C::B) ? bi * C::B + tid : bj * C::B + (tid - C::B);
+            s.col[tid] = lc < cols ? (sorted ? s.ord[lc] : lc) : -1;
           }
           __syncthreads();
-          gram<T, W2>(s, Wsl, rows, rows);
-          inner_sweep<T, W2>(s, tol, round == 0);
+          gram<T, W2, NS>(s, Wsl, rows, rows);
+          for (int is = 0; is < p.inner_sweeps; ++is) {
+            inner_sweep<T, W2, NS>(s, tol, round == 0 || is > 0, is == 0);
+            if (!s.step_rot) break;
+          }
+          __syncthreads();
+          if (sorted && tid < W2 && s.col[tid] >= 0)     // squared norms after this step
+            __stcg(p.norm2 + (int64_t)slice * cols + s.col[tid], (float)s.G[tid * C::LDG + tid]);
           if (s.any_rot) {
             if (tid == 0) s.sweep_any = 1;
-            apply_q<T, W2>(s, Wsl, rows, rows);
-            apply_q<T, W2>(s, Vsl, cols, cols);
+            apply_q<T, W2, NS>(s, Wsl, rows, rows);
+            apply_q<T, W2, NS>(s, Vsl, cols, cols);
           }
           __syncthreads();
         }
@@ -452,11 +505,11 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiParams p) {
   cluster.sync();  // keep shared memory alive until every CTA has read the slice index
 }
 
-template <typename T, int W2>
+template <typename T, int W2, int NS>
 cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hint,
                           int grid_hint) {
-  auto kern = jacobi_kernel<T, W2>;
-  size_t smem = sizeof(Smem<T, W2>);
+  auto kern = jacobi_kernel<T, W2, NS>;
+  size_t smem = sizeof(Smem<T, W2, NS>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -649,12 +702,16 @@ __global__ void transpose_kernel(const T *__restrict__ A, int64_t m, int64_t p, 
 
 template <typename T>
 cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, int cluster_hint,
-                       int grid_hint) {
+                       int grid_hint, int stages) {
   int w = width_hint;
   if (w != 16 && w != 32 && w != 64) w = p.cols <= 8 ? 16 : (p.cols <= 16 || p.cols < 256 ? 32 : 64);
-  if (w == 16) return launch_jacobi<T, 16>(p, st, cluster_hint, grid_hint);
-  if (w == 32) return launch_jacobi<T, 32>(p, st, cluster_hint, grid_hint);
-  return launch_jacobi<T, 64>(p, st, cluster_hint, grid_hint);
+  const bool two = stages == 2 || (stages == 0 && w == 64);
+  if (w == 16) return two ? launch_jacobi<T, 16, 2>(p, st, cluster_hint, grid_hint)
+                          : launch_jacobi<T, 16, 3>(p, st, cluster_hint, grid_hint);
+  if (w == 32) return two ? launch_jacobi<T, 32, 2>(p, st, cluster_hint, grid_hint)
+                          : launch_jacobi<T, 32, 3>(p, st, cluster_hint, grid_hint);
+  return two ? launch_jacobi<T, 64, 2>(p, st, cluster_hint, grid_hint)
+             : launch_jacobi<T, 64, 3>(p, st, cluster_hint, grid_hint);
 }
 
 template <typename T>
@@ -693,7 +750,7 @@ cudaError_t transpose_slices(const T *A, int64_t m, int64_t p, int64_t nslices, 
 }
 
 #define INST(T)                                                                               \
-  template cudaError_t jacobi_run<T>(const JacobiParams &, cudaStream_t, int, int, int);      \
+  template cudaError_t jacobi_run<T>(const JacobiParams &, cudaStream_t, int, int, int, int); \
   template cudaError_t jacobi_finalize<T>(const T *, int64_t, int, int, int, T *, int *,      \
                                           cudaStream_t);                                      \
   template cudaError_t emit_factors<T>(const T *, int64_t, const T *, int64_t, int, int, int, \

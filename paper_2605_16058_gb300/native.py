@@ -26,7 +26,7 @@ SIGNATURES = {
     "tsvdm_plan_create": (_i32, [_i64, _i64, _i64, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
     "tsvdm_plan_destroy": (_i32, [_vp]),
     "tsvdm_plan_set_jacobi": (_i32, [_vp, _dbl, _i32]),
-    "tsvdm_plan_set_tuning": (_i32, [_vp, _i32, _i32, _i32]),
+    "tsvdm_plan_set_tuning": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
     "tsvdm_transform": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "tsvdm_fixed_rank": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pdbl]),
     "tsvdm_tolerance": (_i32, [_vp, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _vp, _i64, _pi64, _pdbl]),
@@ -107,9 +107,12 @@ def tsvdm_plan_set_jacobi(plan, tol, max_sweeps):
                  "tsvdm_plan_set_jacobi")
 
 
-def tsvdm_plan_set_tuning(plan, block_width=0, cluster_size=0, clusters=0):
+def tsvdm_plan_set_tuning(plan, block_width=0, cluster_size=0, clusters=0, stages=0, ordering=0,
+                          inner_sweeps=0):
     return check(lib().tsvdm_plan_set_tuning(plan, int(block_width), int(cluster_size),
-                                             int(clusters)), "tsvdm_plan_set_tuning")
+                                             int(clusters), int(stages), int(ordering),
+                                             int(inner_sweeps)),
+                 "tsvdm_plan_set_tuning")
 
 
 def tsvdm_transform(plan, X, M, inverse, Y):
