@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--workload", default="climate", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16x3"],
+                    help="TTM arithmetic (the slice SVDs run in FP32 in every mode)")
     return ap.parse_args()
 
 
@@ -185,7 +188,7 @@ def main():
     X = Xh.cuda()
     M = Mh.cuda()
     stream = torch.cuda.current_stream()
-    plan = Plan(n1, n2, n3, dtype=torch.float32, orthogonal=True, stream=stream)
+    plan = Plan(n1, n2, n3, dtype=torch.float32, prec=args.prec, orthogonal=True, stream=stream)
     cap = n3 * r
     ranks = torch.empty(n3, dtype=torch.int32, device="cuda")
     offs = torch.empty(n3 + 1, dtype=torch.int64, device="cuda")
@@ -263,14 +266,14 @@ def main():
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = alg_flops / (jac_ms * 1e-3) / 1e12
     ttm_ms = statistics.mean(s["ttm"] for s in stage_ms)
-    ttm_gbs = (2 * n1 * n2 * n3 * 4 + n3 * n3 * 4) / (ttm_ms * 1e-3) / 1e9
+    ttm_gbs = (2 * n1 * n2 * n3 * 4 + n3 * n3 * 4) / (ttm_ms * 1e-3) / 1e9   # incl. B prep
     stages = {k: round(statistics.mean(s[k] for s in stage_ms), 3) for k in native.STAGES}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "slices_per_s": slices_s,
+        "slices_per_s": slices_s, "ttm_precision": args.prec,
         "config": {"workload": desc, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "input %.0f MB%s" % (n1 * n2 * n3 * 4 / 1e6, " > 129 MB L2, no flush"
                                                if n1 * n2 * n3 * 4 > 129e6 else ""), "total_rank": int(tot),
@@ -289,6 +292,22 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
     }
+    if not args.no_learned:
+        # fwd+bwd of the learned Cayley transform: crystal-shaped 512x256x128 FP32, k = 16,
+        # 50 Adam steps at lr 1e-3 (every step: Cayley, t-SVDM-I, backward, adjoint, Adam)
+        from paper_2605_16058_gb300.learn import CayleyTrainer
+        cs = (512, 256, 128)
+        Xc = synth.crystal(shape=cs, seed=4)
+        Xcd = torch.from_numpy(np.ascontiguousarray(Xc.transpose(2, 1, 0))).cuda()
+        M0 = torch.from_numpy(np.ascontiguousarray(synth.dct2_matrix(cs[2]).T.astype(np.float32))).cuda()
+        tr = CayleyTrainer(Xcd, M0, cs, 16, lr=1e-3)
+        tr.train(3, record=False)                        # warm-up (3 steps, then restart)
+        tr = CayleyTrainer(Xcd, M0, cs, 16, lr=1e-3)
+        losses, ms_ls = tr.train(50)
+        line["learned_m"] = {"workload": "crystal-shaped 512x256x128 FP32, Cayley(DCT-II), "
+                                         "k=16, 50 Adam steps lr=1e-3",
+                             "fwd_bwd_ms_per_step": ms_ls, "loss_first": losses[0],
+                             "loss_last": losses[-1]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         ns = min(cores, n3)

@@ -1,0 +1,123 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark times.
+
+  climate 1024x512x365 FP32, DCT-II, t-SVDM-II eps = 1e-2 (the benchmark workload):
+    * ranks equal Algorithm 2 applied (FP64, oracle) to the GPU's own singular values;
+    * the reported error is below eps and equals sqrt(discarded / total) of those values;
+    * sampled slices: the oracle's FP64 TTM + Jacobi SVD of the slice gives the same
+      singular values (1e-5 sigma_max) and the same kept subspaces (projector 1e-4 where
+      the gap exceeds 1e-2 sigma_max).
+  cfd 2048x256x512 FP32, DCT-II, t-SVDM-I k = 32 with the BF16x3 and TF32 tensor-core TTMs:
+    sampled slices against the oracle as above, and the BF16x3 relative error within 1e-5
+    of the FP32 CUDA-core path's.
+  crystal 512x256x128 FP32, DCT-II, k = 16 (learned-transform workload): loss (1e-4) and
+    dL/dM (5e-3, see the test) against the full FP64 oracle.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_16058_gb300 import synth
+
+from helpers import np_lib, proj_diff, t_lib
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_16058_gb300 import build
+    build.build()
+
+
+def _sampled_slices(X, M, which):
+    Ahat = oracle.ttm3(X, M, which=which)
+    U, S, V, sw = oracle.svd_slices(Ahat, threads=len(which))
+    return U, S, V
+
+
+# FP32 rotations leave errors of about u sigma_max in every column, so a subspace whose gap
+# to the rest of the spectrum is g carries an error of about u sigma_max / g; the 1e-4
+# projector bar is therefore applied where the gap exceeds 1e-2 sigma_max.
+# sigma_max is the tensor's largest singular value: the transform's rounding is absolute
+# at that scale (a high-frequency slice that is pure noise comes out of a cancellation).
+def _check_slice(S_o, U_o, s_g, U_g, kk, smax, tol_sig=1e-5, tol_proj=1e-4, gap=1e-2):
+    assert np.max(np.abs(S_o[: len(s_g)] - s_g)) <= tol_sig * smax
+    nxt = S_o[kk] if kk < len(S_o) else 0.0        # beyond the thin SVD: the zero space
+    if kk > 0 and S_o[kk - 1] - nxt > gap * smax:
+        assert proj_diff(U_o[:, :kk], U_g[:, :kk]) <= tol_proj
+
+
+def test_climate_tolerance_full_size():
+    from paper_2605_16058_gb300.tsvdm import Plan
+    n1, n2, n3 = 1024, 512, 365
+    eps = 1e-2
+    X = synth.climate(shape=(n1, n2, n3), seed=1)
+    M = synth.dct2_matrix(n3)
+    plan = Plan(n1, n2, n3, dtype=torch.float32)
+    Xd, Md = t_lib(X), t_lib(M, dtype=torch.float32)
+    out = plan.tolerance(Xd, Md, eps)
+    ranks = out["ranks"].cpu().numpy()
+    off = out["offsets"].cpu().numpy()
+    assert np.array_equal(np.diff(off), ranks) and off[-1] == out["total_rank"]
+    full = plan.fixed_rank(Xd, Md, n2, rel_err=False)         # all singular values
+    S_gpu = np_lib(full["S"])
+    sel = oracle.select_ranks(S_gpu, eps)
+    assert np.array_equal(ranks, sel["ranks"])
+    assert abs(out["rel_err"] - np.sqrt(sel["discarded"] / sel["total"])) <= 1e-12
+    assert out["rel_err"] < eps
+    which = [0, 1, 182, 364]
+    Xs = X.astype(np.float64)
+    U_o, S_o, _ = _sampled_slices(Xs, M.astype(np.float32).astype(np.float64), which)
+    U_pk = out["U"].cpu().double().numpy().T          # n1 x total
+    smax = S_gpu.max()
+    for q, i in enumerate(which):
+        a, b = off[i], off[i + 1]
+        _check_slice(S_o[:, q], U_o[:, :, q], S_gpu[:, i], U_pk[:, a:b], b - a, smax)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_cfd_fixed_rank_full_size(prec):
+    from paper_2605_16058_gb300.tsvdm import Plan
+    n1, n2, n3, k = 2048, 256, 512, 32
+    X = synth.cfd(shape=(n1, n2, n3), seed=3)
+    M = synth.dct2_matrix(n3).astype(np.float32)
+    Xd, Md = t_lib(X), t_lib(M)
+    plan = Plan(n1, n2, n3, dtype=torch.float32, prec=prec)
+    out = plan.fixed_rank(Xd, Md, k)
+    S_g, U_g = np_lib(out["S"]), np_lib(out["U"])
+    which = [0, 7, 255, 511]
+    U_o, S_o, _ = _sampled_slices(X.astype(np.float64), M.astype(np.float64), which)
+    # TF32 products carry ~2^-11 relative error, BF16x3 ~2^-16 (error model of the TTM)
+    tol = 1e-5 if prec == "bf16x3" else 2e-3
+    smax = S_g.max()
+    for q, i in enumerate(which):
+        _check_slice(S_o[:, q], U_o[:, :, q], S_g[:, i], U_g[:, :, i], k, smax, tol_sig=tol,
+                     tol_proj=1e-4 if prec == "bf16x3" else 5e-2,
+                     gap=1e-2 if prec == "bf16x3" else 5e-2)
+    if prec == "bf16x3":
+        ref = Plan(n1, n2, n3, dtype=torch.float32, prec="fp32").fixed_rank(Xd, Md, k)
+        assert abs(out["rel_err"] - ref["rel_err"]) <= 1e-5
+
+
+def test_crystal_loss_and_gradient_full_size():
+    from paper_2605_16058_gb300.tsvdm import Plan
+    n1, n2, n3, k = 512, 256, 128, 16
+    X = synth.crystal(shape=(n1, n2, n3), seed=4)
+    M = synth.dct2_matrix(n3).astype(np.float32)
+    plan = Plan(n1, n2, n3, dtype=torch.float32)
+    Xd, Md = t_lib(X), t_lib(M)
+    f = plan.fixed_rank(Xd, Md, k)
+    dM = torch.empty_like(Md)
+    loss = plan.backward(Xd, Md, k, f["U"], f["S"], f["V"], 1.0, None, dM, "host")
+    g = oracle.loss_and_grad(X.astype(np.float64), M.astype(np.float64), k,
+                             threads=os.cpu_count())
+    assert abs(loss - g["loss"]) <= 1e-4 * g["loss"]
+    # dL/dM = R^T X / (sqrt(E) ||X||) inherits the rank-k subspace error of FP32 Jacobi
+    # (about u sigma_max / gap at k) amplified by 1 / L (L ~ 1e-2 here): a few 1e-3.
+    d = np_lib(dM)
+    assert np.linalg.norm(d - g["dM"]) <= 5e-3 * np.linalg.norm(g["dM"])

@@ -98,7 +98,7 @@ def _compare_factors(dt, S_o, U_o, V_o, S_g, U_g, V_g, k):
         smax = max(so[0], 1e-300)
         assert np.max(np.abs(so[:k] - sg[:k])) <= tol["sig"] * smax, (i, so[:k], sg[:k])
         for kk in range(1, k + 1):
-            gap_next = so[kk - 1] - so[kk] if kk < len(so) else so[kk - 1]
+            gap_next = so[kk - 1] - (so[kk] if kk < len(so) else 0.0)
             if gap_next > tol["gap"] * smax and so[kk - 1] > tol["gap"] * smax:
                 assert proj_diff(U_o[:, :kk, i], U_g[:, :kk, i]) <= tol["proj"], (i, kk)
                 assert proj_diff(V_o[:, :kk, i], V_g[:, :kk, i]) <= tol["proj"], (i, kk)
@@ -200,7 +200,7 @@ def test_tolerance_matches_oracle(dt, shape, eps):
         assert np.max(np.abs(S[a:b] - ref["S_all"][: b - a, i])) <= TOL[dt]["sig"] * max(smax, 1e-300) * 10
         kk = b - a
         so = ref["S_all"][:, i]
-        if kk == len(so) or so[kk - 1] - so[kk] > TOL[dt]["gap"] * smax:
+        if so[kk - 1] - (so[kk] if kk < len(so) else 0.0) > TOL[dt]["gap"] * smax:
             assert proj_diff(full[0][:, :kk, i], U[:, a:b]) <= TOL[dt]["proj"]
 
 
