@@ -55,7 +55,9 @@ typedef enum {
   TSVDM_ENOMEM = 6,      /* device or pinned-host allocation failed                   */
   TSVDM_ECAPACITY = 7,   /* t-SVDM-II: the output capacity is below the total rank    */
   TSVDM_ECUDA = 8,       /* a CUDA runtime call failed                                */
-  TSVDM_ENOTSUP = 9      /* combination not supported (e.g. TF32 precision with F64)  */
+  TSVDM_ENOTSUP = 9,     /* combination not supported (e.g. TF32 precision with F64)  */
+  TSVDM_ESCRATCH = 10    /* the problem exceeds the fixed scratch of an allocation-free
+                            entry point                                               */
 } tsvdm_status;
 
 typedef enum { TSVDM_F32 = 0, TSVDM_F64 = 1 } tsvdm_dtype;
@@ -225,6 +227,29 @@ tsvdm_status tsvdm_cayley_backward(int64_t n, tsvdm_dtype dtype, const void *M0,
 tsvdm_status tsvdm_adam(int64_t count, tsvdm_dtype dtype, void *param, const void *grad,
                         void *m1, void *m2, int64_t step, double lr, double beta1,
                         double beta2, double eps, void *stream);
+
+/* Allocation-free t-SVDM-II rank choice.  The paper has no counterpart: it exists for
+ * callers that must not call cudaMalloc (a process whose device memory is all handed to
+ * another allocator up front, or a service that forbids allocation on its request path
+ * because a driver allocation can synchronise the device and take milliseconds).
+ * Same computation as the selection inside tsvdm_tolerance: Algorithm 2 steps 2-8 on
+ * given singular values, with the sort scratch in a fixed 2 MiB array built into the
+ * library (held on every GPU that loads it until the process exits) instead of a plan.
+ *   sigma    device float [cols x nslices], column i = slice i's singular values sorted
+ *            in descending order (e.g. S of tsvdm_fixed_rank with k = min(n1, n2))
+ *   eps      relative tolerance in (0, 1)
+ *   ranks    device int32 [nslices]; offsets device int64 [nslices + 1] (as tsvdm_tolerance)
+ *   summary  device double [4] or NULL: sum of all sigma^2, sum of discarded sigma^2,
+ *            tau (a sigma^2 value, -1 when nothing is discarded), total rank
+ *   stream   cudaStream_t
+ * At most 262,144 singular values per call (cols * nslices); larger problems return
+ * TSVDM_ESCRATCH without launching anything.  Nothing is allocated.  The first call on a
+ * device looks up the scratch's device address (once per device, with that device
+ * current); make that first call before any stream capture.  Every call shares the
+ * scratch, so calls whose work overlaps on the GPU race: issue them on one stream. */
+tsvdm_status tsvdm_select_ranks_noalloc(const float *sigma, int64_t cols, int64_t nslices,
+                                        double eps, int32_t *ranks, int64_t *offsets,
+                                        double *summary, void *stream);
 
 #ifdef __cplusplus
 }

@@ -402,6 +402,7 @@ const char *tsvdm_strerror(tsvdm_status s) {
     case TSVDM_ECAPACITY: return "output capacity below the total rank";
     case TSVDM_ECUDA: return "CUDA runtime error";
     case TSVDM_ENOTSUP: return "not supported";
+    case TSVDM_ESCRATCH: return "problem exceeds the fixed scratch of the allocation-free entry point";
   }
   return "unknown status";
 }

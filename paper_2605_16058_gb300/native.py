@@ -14,7 +14,7 @@ import threading
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libtsvdm.so")
 
-OK, EINVAL, ENOTORTHO, ENOCONV, ENONFINITE, ETIMEOUT, ENOMEM, ECAPACITY, ECUDA, ENOTSUP = range(10)
+OK, EINVAL, ENOTORTHO, ENOCONV, ENONFINITE, ETIMEOUT, ENOMEM, ECAPACITY, ECUDA, ENOTSUP, ESCRATCH = range(11)
 F32, F64 = 0, 1
 P_FP64, P_FP32, P_TF32, P_BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": P_FP64, "fp32": P_FP32, "tf32": P_TF32, "bf16x3": P_BF16X3}
@@ -40,6 +40,7 @@ SIGNATURES = {
     "tsvdm_cayley_backward": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tsvdm_plan_profile": (_i32, [_vp, _i32]),
     "tsvdm_plan_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_float), _pi64]),
+    "tsvdm_select_ranks_noalloc": (_i32, [_vp, _i64, _i64, _dbl, _vp, _vp, _vp, _vp]),
     "tsvdm_adam": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _i64, _dbl, _dbl, _dbl, _dbl, _vp]),
 }
 

@@ -1,0 +1,70 @@
+"""Allocation-free t-SVDM-II rank choice (tsvdm_select_ranks_noalloc) against the
+existing entry point tsvdm_tolerance, through the C ABI, on two calls in a row.
+
+The allocation-free entry point serves callers that must not call cudaMalloc (a process
+whose device memory is all handed to another allocator, or a request path that forbids
+driver allocations); it keeps its sort scratch in a fixed array inside the library.
+Ranks and offsets are integers and must match exactly; the reported error within 1e-12.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2605_16058_gb300 import synth
+
+from helpers import t_lib
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_16058_gb300 import build
+    build.build()
+
+
+def _noalloc(sig, cols, nslices, eps, ranks, offsets, summary):
+    from paper_2605_16058_gb300 import native
+    st = torch.cuda.current_stream().cuda_stream
+    return native.lib().tsvdm_select_ranks_noalloc(
+        ctypes.c_void_p(sig.data_ptr()), cols, nslices, float(eps),
+        ctypes.c_void_p(ranks.data_ptr()), ctypes.c_void_p(offsets.data_ptr()),
+        ctypes.c_void_p(summary.data_ptr()) if summary is not None else None,
+        ctypes.c_void_p(st))
+
+
+def test_noalloc_selection_matches_tsvdm_tolerance_twice():
+    from paper_2605_16058_gb300 import native
+    from paper_2605_16058_gb300.tsvdm import Plan
+    n1, n2, n3 = 120, 80, 24
+    X = synth.climate(shape=(n1, n2, n3), seed=6)
+    M = synth.dct2_matrix(n3)
+    plan = Plan(n1, n2, n3, dtype=torch.float32)
+    Xd, Md = t_lib(X), t_lib(M, dtype=torch.float32)
+    full = plan.fixed_rank(Xd, Md, n2, rel_err=False)      # sigma, descending per slice
+    sig = full["S"].contiguous()                            # (n3, r) = r x n3 column-major
+    for eps in (2e-2, 2e-2, 1e-3):                          # two identical calls, then another
+        ref = plan.tolerance(Xd, Md, eps)
+        ranks = torch.full((n3,), -1, dtype=torch.int32, device="cuda")
+        offs = torch.full((n3 + 1,), -1, dtype=torch.int64, device="cuda")
+        summ = torch.zeros(4, dtype=torch.float64, device="cuda")
+        assert _noalloc(sig, n2, n3, eps, ranks, offs, summ) == native.OK
+        torch.cuda.synchronize()
+        assert torch.equal(ranks, ref["ranks"])
+        assert torch.equal(offs, ref["offsets"])
+        total, disc, tau, totrank = summ.cpu().tolist()
+        assert int(totrank) == ref["total_rank"]
+        assert abs(np.sqrt(disc / total) - ref["rel_err"]) <= 1e-12
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    from paper_2605_16058_gb300 import native
+    sig = torch.zeros(4, device="cuda")
+    ranks = torch.zeros(4, dtype=torch.int32, device="cuda")
+    offs = torch.zeros(5, dtype=torch.int64, device="cuda")
+    assert _noalloc(sig, 1024, 300, 0.1, ranks, offs, None) == native.ESCRATCH
+    assert _noalloc(sig, 4, 1, 1.5, ranks, offs, None) == native.EINVAL
