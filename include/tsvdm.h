@@ -228,6 +228,51 @@ tsvdm_status tsvdm_adam(int64_t count, tsvdm_dtype dtype, void *param, const voi
                         void *m1, void *m2, int64_t step, double lr, double beta1,
                         double beta2, double eps, void *stream);
 
+/* ---- batches of tensors with uneven shapes (one persistent Jacobi launch, graph) ----
+ * The spec batching extension of t-SVDM-I / t-SVDM-II (Sec. 3.3, Algorithm 2):
+ * count tensors, each with its own n1 x n2 x n3, orthogonal M and mode, decomposed by one
+ * stream of work whose dominant step is a single persistent Jacobi launch over every
+ * slice of every tensor (longest slices first).  Nothing is read back to the host, so the
+ * whole run can be captured once into a CUDA graph (tsvdm_batch_capture) and replayed
+ * (tsvdm_batch_launch).  M must be a multiple of an orthogonal matrix; min(n1,n2) <= 1024. */
+typedef struct {
+  int64_t n1, n2, n3;
+  int mode;        /* 0: t-SVDM-I with rank k; 1: t-SVDM-II with tolerance eps */
+  int64_t k;
+  double eps;
+} tsvdm_batch_desc;
+
+typedef struct {
+  const void *X, *M;   /* device inputs (column-major n1 x n2 x n3, n3 x n3) */
+  void *U, *S, *V;     /* device outputs.  mode 0: U n1 x k x n3, S k x n3, V n2 x k x n3.
+                          mode 1: packed, capacity n3 min(n1,n2) columns (U n1 x cap,
+                          S cap, V n2 x cap), slice i at offsets[i]..offsets[i+1]-1 */
+  int32_t *ranks;      /* mode 1: device [n3] (nullable) */
+  int64_t *offsets;    /* mode 1: device [n3 + 1] (nullable) */
+  double *rel_err;     /* device double (nullable): sqrt(discarded / total sigma^2) */
+} tsvdm_batch_io;
+
+typedef struct tsvdm_batch_s *tsvdm_batch;
+
+/* Allocates the workspace of all tensors (EINVAL for a bad descriptor). */
+tsvdm_status tsvdm_batch_create(const tsvdm_batch_desc *descs, int count, tsvdm_dtype dtype,
+                                tsvdm_prec prec, void *stream, tsvdm_batch *out);
+tsvdm_status tsvdm_batch_destroy(tsvdm_batch b);
+/* Enqueues one decomposition of every tensor (io[count]) on the batch's stream. */
+tsvdm_status tsvdm_batch_run(tsvdm_batch b, const tsvdm_batch_io *io);
+/* Runs once, then captures one run into a CUDA graph (io pointers are baked in).  The
+ * batch must have been created on a non-default stream (EINVAL otherwise). */
+tsvdm_status tsvdm_batch_capture(tsvdm_batch b, const tsvdm_batch_io *io);
+/* Replays the captured graph on the batch's stream. */
+tsvdm_status tsvdm_batch_launch(tsvdm_batch b);
+/* Autotuner: times the Jacobi launch for each candidate (block width 32/64, cluster size
+ * 1/2/4, pipeline stages 2/3) on these inputs and keeps the fastest; choice (nullable,
+ * int[4]) receives width, cluster size, stages and the best time in microseconds. */
+tsvdm_status tsvdm_batch_tune(tsvdm_batch b, const tsvdm_batch_io *io, int *choice);
+/* Synchronises; sweeps and rotations summed over all slices of the last run, and the
+ * device-detected status (ENOCONV, ENONFINITE, ETIMEOUT or OK, then cleared). */
+tsvdm_status tsvdm_batch_status(tsvdm_batch b, int64_t *sweeps, int64_t *rotations);
+
 /* Allocation-free t-SVDM-II rank choice.  The paper has no counterpart: it exists for
  * callers that must not call cudaMalloc (a process whose device memory is all handed to
  * another allocator up front, or a service that forbids allocation on its request path

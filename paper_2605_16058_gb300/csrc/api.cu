@@ -10,12 +10,6 @@
 
 using namespace tsvdm;
 
-namespace tsvdm {
-template <typename T>
-cudaError_t trunc_sums(const T *sig, int cols, int nslices, int64_t k, double *scal,
-                       cudaStream_t st);
-}
-
 enum { SC_INVSCALE = 9 };
 enum { STG_X = 0, STG_M, STG_U, STG_S, STG_V, STG_RANKS, STG_OFF, STG_COUNT };
 
@@ -200,6 +194,7 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   jp.rots = p->rots;
   jp.norm2 = p->sort_cols ? p->norm2 : nullptr;
   jp.inner_sweeps = p->inner_sweeps;
+  jp.desc = nullptr;
   stage_begin(p, TSVDM_STAGE_JACOBI);
   CK(jacobi_run<T>(jp, p->st, p->width_hint, p->cluster_hint, p->grid_hint, p->stages_hint));
   stage_end(p, TSVDM_STAGE_JACOBI, 1);

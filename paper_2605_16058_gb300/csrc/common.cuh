@@ -54,6 +54,16 @@ template <typename T>
 cudaError_t transpose_slices(const T *A, int64_t m, int64_t p, int64_t nslices, T *B,
                              cudaStream_t st);
 
+// One slice of a batched decomposition (tensors of different shapes in one launch).
+struct SliceDesc {
+  void *A;             // rows x cols work matrix (column-major, lda = rows)
+  void *V;             // cols x cols rotations
+  float *norm2;        // cols squared norms (de Rijk ordering)
+  void *sig;           // cols sorted singular values (finalize output)
+  int *perm;           // cols column permutation (finalize output)
+  int rows, cols;
+};
+
 struct JacobiParams {
   void *A;             // slice s work matrix at A + s*sA: rows x cols, column-major
   void *V;             // slice s rotations at V + s*sV: cols x cols
@@ -68,6 +78,7 @@ struct JacobiParams {
   long long *rots;     // [nslices] rotations applied
   float *norm2;        // [nslices * cols] squared column norms (nullptr: natural order)
   int inner_sweeps;    // Gram sweeps per block pair (>= 1)
+  const SliceDesc *desc; // per-slice matrices (batched), or nullptr (uniform, A/V/sA/sV)
 };
 
 template <typename T>
@@ -78,6 +89,10 @@ cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, i
 template <typename T>
 cudaError_t jacobi_finalize(const T *A, int64_t sA, int rows, int cols, int nslices, T *sig,
                             int *perm, cudaStream_t st);
+
+template <typename T>
+cudaError_t jacobi_finalize_desc(const SliceDesc *desc, int nslices, int max_cols,
+                                 cudaStream_t st);
 
 // Writes normalised, sign-fixed factors of slices (see emit in jacobi.cu).
 template <typename T>
@@ -90,6 +105,22 @@ cudaError_t emit_factors(const T *A, int64_t sA, const T *Vw, int64_t sV, int ro
 template <typename T>
 cudaError_t select_ranks(const T *sig, int cols, int nslices, double eps, void *keys_ws,
                          double *scal, int *ranks, int64_t *offsets, cudaStream_t st);
+
+// The selection of one t-SVDM-II tensor of a batch (one CTA each).
+struct SelectSeg {
+  const void *sig;     // cols x nslices, descending per slice
+  int cols, nslices;
+  double eps;
+  void *keys;          // 2 * cols * nslices 64-bit keys
+  double *scal;        // SC_COUNT scalars
+  int *ranks;
+  int64_t *offsets;
+};
+template <typename T>
+cudaError_t select_segments(const SelectSeg *segs, int count, cudaStream_t st);
+template <typename T>
+cudaError_t trunc_sums(const T *sig, int cols, int nslices, int64_t k, double *scal,
+                       cudaStream_t st);
 
 // Per-slice product Out_i = [Base_i -] U_i diag(S_i) V_i^T.
 template <typename T>

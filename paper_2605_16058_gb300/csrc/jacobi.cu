@@ -151,7 +151,7 @@ __device__ void gram(Smem<T, W2, NS> &s, const T *__restrict__ Wsl, int rows, in
   const int kg = tid / C::TILES;
   const int tile = tid % C::TILES;
   const int ti = tile / C::TD, tj = tile % C::TD;
-  const bool aligned = (lda % C::VN) == 0;
+  const bool aligned = (lda % C::VN) == 0 && ((uintptr_t)Wsl & 15) == 0;
   const int nck = (rows + C::RC - 1) / C::RC;
   T acc[4][4];
 #pragma unroll
@@ -339,7 +339,7 @@ __device__ void apply_q(Smem<T, W2, NS> &s, T *__restrict__ Wsl, int rows, int l
   using C = Cfg<T, W2, NS>;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const bool aligned = (lda % C::VN) == 0;
+  const bool aligned = (lda % C::VN) == 0 && ((uintptr_t)Wsl & 15) == 0;
   const int nck = (rows + C::RC - 1) / C::RC;
   const int j0 = warp * C::CPW;
 #pragma unroll
@@ -398,10 +398,6 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
   const int crank = (int)cluster.block_rank();
   const int csize = (int)cluster.num_blocks();
   const int tid = threadIdx.x;
-  const int rows = p.rows, cols = p.cols;
-  int nb = (cols + C::B - 1) / C::B;
-  if (nb & 1) ++nb;
-  if (nb < 2) nb = 2;
   const double tol = p.tol;
 
   for (int iter = 0;; ++iter) {
@@ -410,8 +406,27 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
     cluster.sync();
     const int slice = *cluster.map_shared_rank(&s.slice[par], 0);
     if (slice >= p.nslices) break;
-    T *Wsl = reinterpret_cast<T *>(p.A) + (int64_t)slice * p.sA;
-    T *Vsl = reinterpret_cast<T *>(p.V) + (int64_t)slice * p.sV;
+    // this slice's matrices: uniform batch of one tensor, or a per-slice descriptor
+    T *Wsl, *Vsl;
+    float *nrm2;
+    int rows, cols;
+    if (p.desc) {
+      const SliceDesc d = p.desc[slice];
+      Wsl = reinterpret_cast<T *>(d.A);
+      Vsl = reinterpret_cast<T *>(d.V);
+      nrm2 = d.norm2;
+      rows = d.rows;
+      cols = d.cols;
+    } else {
+      Wsl = reinterpret_cast<T *>(p.A) + (int64_t)slice * p.sA;
+      Vsl = reinterpret_cast<T *>(p.V) + (int64_t)slice * p.sV;
+      nrm2 = p.norm2 ? p.norm2 + (int64_t)slice * p.cols : nullptr;
+      rows = p.rows;
+      cols = p.cols;
+    }
+    int nb = (cols + C::B - 1) / C::B;
+    if (nb & 1) ++nb;
+    if (nb < 2) nb = 2;
 
     // V = I (this CTA initialises columns crank, crank + csize, ...)
     for (int c = crank; c < cols; c += csize)
@@ -422,7 +437,7 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
     }
     cluster.sync();
 
-    const bool sorted = p.norm2 != nullptr && cols <= MAXSORT;
+    const bool sorted = nrm2 != nullptr && cols <= MAXSORT;
     int converged = 0, sweep = 0;
     for (sweep = 1; sweep <= p.max_sweeps; ++sweep) {
       if (tid == 0) s.sweep_any = 0;
@@ -432,7 +447,7 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
         int p2 = 1;
         while (p2 < cols) p2 <<= 1;
         float *key = reinterpret_cast<float *>(s.buf);
-        const float *nrm = p.norm2 + (int64_t)slice * cols;
+        const float *nrm = nrm2;
         for (int c = tid; c < p2; c += NT) {
           key[c] = c < cols ? (sweep == 1 ? -(float)c : __ldcg(nrm + c)) : -INFINITY;
           s.ord[c] = c;
@@ -472,7 +487,7 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
           }
           __syncthreads();
           if (sorted && tid < W2 && s.col[tid] >= 0)     // squared norms after this step
-            __stcg(p.norm2 + (int64_t)slice * cols + s.col[tid], (float)s.G[tid * C::LDG + tid]);
+            __stcg(nrm2 + s.col[tid], (float)s.G[tid * C::LDG + tid]);
           if (s.any_rot) {
             if (tid == 0) s.sweep_any = 1;
             apply_q<T, W2, NS>(s, Wsl, rows, rows);
@@ -553,12 +568,23 @@ cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hi
 template <typename T>
 __global__ void __launch_bounds__(256) finalize_kernel(const T *__restrict__ A, int64_t sA,
                                                        int rows, int cols, T *sig, int *perm,
-                                                       int p2) {
+                                                       int p2, const SliceDesc *desc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *key = reinterpret_cast<T *>(smem_raw);
   int *idx = reinterpret_cast<int *>(key + p2);
-  const int slice = blockIdx.x;
+  int slice = blockIdx.x;
   const T *W = A + (int64_t)slice * sA;
+  if (desc) {                       // batched: each slice carries its own matrices
+    const SliceDesc d = desc[blockIdx.x];
+    W = reinterpret_cast<const T *>(d.A);
+    rows = d.rows;
+    cols = d.cols;
+    sig = reinterpret_cast<T *>(d.sig);
+    perm = d.perm;
+    slice = 0;
+    p2 = 1;
+    while (p2 < cols) p2 <<= 1;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = warp; j < p2; j += 8) {
     T acc = T(0);
@@ -725,7 +751,22 @@ cudaError_t jacobi_finalize(const T *A, int64_t sA, int rows, int cols, int nsli
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<nslices, 256, smem, st>>>(A, sA, rows, cols, sig, perm, p2);
+  kern<<<nslices, 256, smem, st>>>(A, sA, rows, cols, sig, perm, p2, nullptr);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t jacobi_finalize_desc(const SliceDesc *desc, int nslices, int max_cols,
+                                 cudaStream_t st) {
+  int p2 = 1;
+  while (p2 < max_cols) p2 <<= 1;
+  size_t smem = (size_t)p2 * (sizeof(T) + sizeof(int));
+  auto kern = finalize_kernel<T>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<nslices, 256, smem, st>>>(nullptr, 0, 0, 0, nullptr, nullptr, p2, desc);
   return cudaGetLastError();
 }
 
@@ -753,6 +794,7 @@ cudaError_t transpose_slices(const T *A, int64_t m, int64_t p, int64_t nslices, 
   template cudaError_t jacobi_run<T>(const JacobiParams &, cudaStream_t, int, int, int, int); \
   template cudaError_t jacobi_finalize<T>(const T *, int64_t, int, int, int, T *, int *,      \
                                           cudaStream_t);                                      \
+  template cudaError_t jacobi_finalize_desc<T>(const SliceDesc *, int, int, cudaStream_t);    \
   template cudaError_t emit_factors<T>(const T *, int64_t, const T *, int64_t, int, int, int, \
                                        bool, const T *, const int *, int64_t, const int *,    \
                                        const int64_t *, T *, T *, T *, cudaStream_t);         \

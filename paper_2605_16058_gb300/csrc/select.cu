@@ -93,10 +93,8 @@ __device__ long long block_scan_ll(long long v, long long *wsum, long long *tota
 }
 
 template <typename T>
-__global__ void __launch_bounds__(ST, 1) select_kernel(const T *__restrict__ sig, int cols,
-                                                       int nslices, double eps, void *kws,
-                                                       double *scal, int *ranks,
-                                                       int64_t *offsets) {
+__device__ void select_body(const T *__restrict__ sig, int cols, int nslices, double eps,
+                            void *kws, double *scal, int *ranks, int64_t *offsets) {
   using KO = KeyOf<T>;
   using K = typename KO::K;
   __shared__ int wc[NW * 256];
@@ -280,7 +278,32 @@ __global__ void __launch_bounds__(ST) trunc_sums_kernel(const T *__restrict__ si
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(ST, 1) select_kernel(const T *__restrict__ sig, int cols,
+                                                       int nslices, double eps, void *kws,
+                                                       double *scal, int *ranks,
+                                                       int64_t *offsets) {
+  select_body<T>(sig, cols, nslices, eps, kws, scal, ranks, offsets);
+}
+
+// One CTA per segment (one t-SVDM-II tensor of a batch).
+template <typename T>
+__global__ void __launch_bounds__(ST, 1) select_seg_kernel(const SelectSeg *segs) {
+  const SelectSeg g = segs[blockIdx.x];
+  select_body<T>(reinterpret_cast<const T *>(g.sig), g.cols, g.nslices, g.eps, g.keys, g.scal,
+                 g.ranks, g.offsets);
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t select_segments(const SelectSeg *segs, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  select_seg_kernel<T><<<count, ST, 0, st>>>(segs);
+  return cudaGetLastError();
+}
+template cudaError_t select_segments<float>(const SelectSeg *, int, cudaStream_t);
+template cudaError_t select_segments<double>(const SelectSeg *, int, cudaStream_t);
 
 template <typename T>
 cudaError_t trunc_sums(const T *sig, int cols, int nslices, int64_t k, double *scal,

@@ -40,6 +40,13 @@ SIGNATURES = {
     "tsvdm_cayley_backward": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tsvdm_plan_profile": (_i32, [_vp, _i32]),
     "tsvdm_plan_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_float), _pi64]),
+    "tsvdm_batch_create": (_i32, [_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "tsvdm_batch_destroy": (_i32, [_vp]),
+    "tsvdm_batch_run": (_i32, [_vp, _vp]),
+    "tsvdm_batch_capture": (_i32, [_vp, _vp]),
+    "tsvdm_batch_launch": (_i32, [_vp]),
+    "tsvdm_batch_tune": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "tsvdm_batch_status": (_i32, [_vp, _pi64, _pi64]),
     "tsvdm_select_ranks_noalloc": (_i32, [_vp, _i64, _i64, _dbl, _vp, _vp, _vp, _vp]),
     "tsvdm_adam": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _i64, _dbl, _dbl, _dbl, _dbl, _vp]),
 }
@@ -189,6 +196,56 @@ def tsvdm_plan_profile_read(plan):
     n = ctypes.c_int64(0)
     check(lib().tsvdm_plan_profile_read(plan, ms, ctypes.byref(n)), "tsvdm_plan_profile_read")
     return dict(zip(STAGES, [float(x) for x in ms])), n.value
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int64), ("n2", ctypes.c_int64), ("n3", ctypes.c_int64),
+                ("mode", ctypes.c_int), ("k", ctypes.c_int64), ("eps", ctypes.c_double)]
+
+
+class BatchIO(ctypes.Structure):
+    _fields_ = [("X", _vp), ("M", _vp), ("U", _vp), ("S", _vp), ("V", _vp),
+                ("ranks", _vp), ("offsets", _vp), ("rel_err", _vp)]
+
+
+def tsvdm_batch_create(descs, dtype, prec, stream=None):
+    arr = (BatchDesc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    check(lib().tsvdm_batch_create(arr, len(descs), dtype, prec, _stream(stream),
+                                   ctypes.byref(h)), "tsvdm_batch_create")
+    return h
+
+
+def _io_array(ios):
+    return (BatchIO * len(ios))(*ios)
+
+
+def tsvdm_batch_run(b, ios):
+    return check(lib().tsvdm_batch_run(b, _io_array(ios)), "tsvdm_batch_run")
+
+
+def tsvdm_batch_capture(b, ios):
+    return check(lib().tsvdm_batch_capture(b, _io_array(ios)), "tsvdm_batch_capture")
+
+
+def tsvdm_batch_launch(b):
+    return check(lib().tsvdm_batch_launch(b), "tsvdm_batch_launch")
+
+
+def tsvdm_batch_tune(b, ios):
+    ch = (ctypes.c_int * 4)()
+    check(lib().tsvdm_batch_tune(b, _io_array(ios), ch), "tsvdm_batch_tune")
+    return dict(width=ch[0], cluster=ch[1], stages=ch[2], jacobi_ms=ch[3] / 1000.0)
+
+
+def tsvdm_batch_status(b):
+    a, c = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = lib().tsvdm_batch_status(b, ctypes.byref(a), ctypes.byref(c))
+    return st, a.value, c.value
+
+
+def tsvdm_batch_destroy(b):
+    return lib().tsvdm_batch_destroy(b)
 
 
 def tsvdm_cayley(n, dtype, A, M0, M, Z, Q, work, stream=None):
