@@ -40,6 +40,11 @@ WORKLOADS = {
                        "t-SVDM-II climate-shaped 1024x512x48 FP32, DCT-II, eps=1e-2"),
     "climate-small": ((256, 128, 64), 1e-2,
                       "t-SVDM-II climate-shaped 256x128x64 FP32, DCT-II, eps=1e-2"),
+    # 64 uneven CP tensors (n1 128..1024, n2 64..512, n3 8..128), Haar M, even t-SVDM-I
+    # k=16 / odd t-SVDM-II eps=1e-3, one graph-captured batch (see run_batch_bench)
+    "batch": (None, None, "64 uneven tensors, t-SVDM-I k=16 / t-SVDM-II eps=1e-3, Haar M, "
+                          "one CUDA-graph batch"),
+    "batch-small": (None, None, "8 uneven tensors (first 8 of the 64-tensor batch), graph"),
 }
 FP32_LANES_PER_SM = 128
 SMS = 152
@@ -57,6 +62,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16x3"],
                     help="TTM arithmetic (the slice SVDs run in FP32 in every mode)")
+    ap.add_argument("--fp64-compare", action="store_true",
+                    help="batch workload: also time the all-FP64 GPU path on the same inputs")
     return ap.parse_args()
 
 
@@ -126,14 +133,130 @@ def cpu_sample(X, M, nslices, threads):
     return time.perf_counter() - t0
 
 
+def batch_inputs(count):
+    """Seeded inputs of the uneven batch (first `count` of the 64 shapes)."""
+    from paper_2605_16058_gb300 import synth
+    shapes = synth.batch_shapes()[:count]
+    return [(sh, synth.batch_item(i, sh)) for i, sh in enumerate(shapes)]
+
+
+def run_batch_bench(args, world, rank, local):
+    """All tensors of the batch in one CUDA graph (TTMs, one persistent Jacobi launch over
+    every slice, grouped finalize/selection, emission); value = input GB/s of the replay."""
+    import numpy as np
+    import torch
+    from paper_2605_16058_gb300 import build, native as N
+
+    build.build()
+    torch.cuda.set_device(local)
+    count = 64 if args.workload == "batch" else 8
+    items = batch_inputs(count)
+    stream = torch.cuda.Stream()
+
+    def make(dtype, prec):
+        tdt = torch.float32 if dtype == N.F32 else torch.float64
+        descs, ios, keep = [], [], []
+        for idx, (sh, it) in enumerate(items):
+            n1, n2, n3 = sh
+            r = min(n1, n2)
+            X = torch.from_numpy(np.ascontiguousarray(it["X"].transpose(2, 1, 0))).to(tdt).cuda()
+            M = torch.from_numpy(np.ascontiguousarray(it["M"].T)).to(tdt).cuda()
+            if it["mode"] == "fixed":
+                descs.append(N.BatchDesc(n1, n2, n3, 0, it["k"], 0.0))
+                U = torch.empty(n3, it["k"], n1, dtype=tdt, device="cuda")
+                S = torch.empty(n3, it["k"], dtype=tdt, device="cuda")
+                V = torch.empty(n3, it["k"], n2, dtype=tdt, device="cuda")
+                rk = of = None
+            else:
+                descs.append(N.BatchDesc(n1, n2, n3, 1, 0, it["eps"]))
+                U = torch.empty(n3 * r, n1, dtype=tdt, device="cuda")
+                S = torch.empty(n3 * r, dtype=tdt, device="cuda")
+                V = torch.empty(n3 * r, n2, dtype=tdt, device="cuda")
+                rk = torch.empty(n3, dtype=torch.int32, device="cuda")
+                of = torch.empty(n3 + 1, dtype=torch.int64, device="cuda")
+            rel = torch.zeros(1, dtype=torch.float64, device="cuda")
+            p = lambda t: None if t is None else t.data_ptr()
+            ios.append(N.BatchIO(X.data_ptr(), M.data_ptr(), U.data_ptr(), S.data_ptr(),
+                                 V.data_ptr(), p(rk), p(of), rel.data_ptr()))
+            keep.append((X, M, U, S, V, rk, of, rel))
+        torch.cuda.synchronize()
+        b = N.tsvdm_batch_create(descs, dtype, prec, stream)
+        return b, ios, keep
+
+    def timed(b, steps, warmup):
+        for _ in range(max(3, warmup)):
+            N.tsvdm_batch_launch(b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            N.tsvdm_batch_launch(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    in_bytes = sum(sh[0] * sh[1] * sh[2] * 4 for sh, _ in items)
+    nslices = sum(sh[2] for sh, _ in items)
+    b, ios, keep = make(N.F32, N.PRECISIONS[args.prec])
+    choice = N.tsvdm_batch_tune(b, ios)
+    N.tsvdm_batch_capture(b, ios)
+    clk = Clocks(local)
+    ms = timed(b, args.steps, args.warmup)
+    clocks = clk.stop()
+    st, sweeps, rots = N.tsvdm_batch_status(b)
+    alg, mp_sum = 0.0, 0.0
+    for sh, _ in items:
+        m_, p_ = max(sh[0], sh[1]), min(sh[0], sh[1])
+        alg += sh[2] * 3.0 * m_ * p_ * (p_ - 1)       # dots of one sweep, every slice
+        mp_sum += sh[2] * (m_ + p_)
+    mean_sw = sweeps / nslices
+    # algorithmic flops: dots of every executed sweep (mean sweeps per slice) plus
+    # 6 (m + p) per applied rotation (slice-averaged m + p)
+    alg_flops = alg * mean_sw + rots * 6.0 * mp_sum / nslices
+    pk, src = peaks()
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    rels = [float(k[7].item()) for k in keep]
+    line = {
+        "metric": METRIC, "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "slices_per_s": nslices / (ms * 1e-3), "ttm_precision": args.prec,
+        "config": {"workload": WORKLOADS[args.workload][2], "tensors": len(items),
+                   "slices": nslices, "input_bytes": in_bytes, "status": int(st),
+                   "jacobi_sweeps_mean": mean_sw, "autotuned": choice,
+                   "max_rel_err_tol_items": max(r for (sh, it), r in zip(items, rels)
+                                                if it["mode"] == "tol")},
+        "roofline": {"bound": "alu", "kernel": "jacobi", "unit": "TFLOP/s", "peak": fp32_peak,
+                     "kernel_ms": choice["jacobi_ms"],
+                     "algorithmic_flops": alg_flops,
+                     "achieved": alg_flops / (choice["jacobi_ms"] * 1e-3) / 1e12},
+        "clocks": clocks, "gpu_launches": None,
+    }
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / fp32_peak
+    N.tsvdm_batch_destroy(b)
+    if args.fp64_compare:
+        b64, ios64, keep64 = make(N.F64, N.P_FP64)
+        N.tsvdm_batch_run(b64, ios64)
+        N.tsvdm_batch_capture(b64, ios64)
+        ms64 = timed(b64, 1, 0)
+        line["fp64_gpu_ms_per_step"] = ms64
+        line["speedup_vs_fp64_gpu"] = ms64 / ms
+        N.tsvdm_batch_destroy(b64)
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, wl):
     import numpy as np
     import oracle
     from paper_2605_16058_gb300 import synth
-    (n1, n2, n3), eps, desc = wl
-    X = synth.climate(shape=(n1, n2, n3), seed=1)
-    M = synth.dct2_matrix(n3)
+    (n1, n2, n3), eps, desc = wl if wl[0] else ((None, None, None), None, wl[2])
     cores = os.cpu_count() or 1
+    if n1 is None:                       # batch: sample slices of the first tensor
+        (n1, n2, n3), it = batch_inputs(1)[0]
+        X, M = it["X"], it["M"]
+    else:
+        X = synth.climate(shape=(n1, n2, n3), seed=1)
+        M = synth.dct2_matrix(n3)
     ns = min(cores, n3)
     oracle.build_oracle()
     for _ in range(max(0, args.warmup)):
@@ -165,6 +288,9 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, wl)
+        return
+    if args.workload.startswith("batch"):
+        run_batch_bench(args, world, rank, local)
         return
 
     import numpy as np
