@@ -36,6 +36,8 @@ WORKLOADS = {
     # name: (shape, eps, description)
     "climate": ((1024, 512, 365), 1e-2,
                 "t-SVDM-II climate-shaped 1024x512x365 FP32, DCT-II, eps=1e-2"),
+    "climate-128": ((1024, 512, 128), 1e-2,
+                    "t-SVDM-II climate-shaped 1024x512x128 FP32, DCT-II, eps=1e-2"),
     "climate-medium": ((1024, 512, 48), 1e-2,
                        "t-SVDM-II climate-shaped 1024x512x48 FP32, DCT-II, eps=1e-2"),
     "climate-small": ((256, 128, 64), 1e-2,
@@ -120,6 +122,24 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def jacobi_traffic_per_slice():
+    """DRAM bytes per slice of the Jacobi kernel from the committed ncu summary, or None
+    when the kernel source changed since those counters were taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "jacobi_kernel_climate_1024x512x128.md")
+    src = os.path.join(ROOT, "paper_2605_16058_gb300", "csrc", "jacobi.cu")
+    try:
+        txt = open(prof).read()
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    vals = dict(l.split(":", 1) for l in txt.splitlines()
+                if l.startswith(("dram_bytes_per_slice:", "jacobi_source_sha1:")))
+    if vals.get("jacobi_source_sha1", "").strip() != sha:
+        return None
+    return float(vals["dram_bytes_per_slice"])
 
 
 def cpu_sample(X, M, nslices, threads):
@@ -407,7 +427,9 @@ def main():
                    "jacobi_sweeps_mean": sweeps / n3, "jacobi_rotations": int(rots)},
         "roofline": {"bound": "alu", "kernel": "jacobi", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": None,
+                     "traffic": (None if jacobi_traffic_per_slice() is None
+                                 else jacobi_traffic_per_slice() * n3),
+                     "traffic_note": "ncu dram bytes per slice (1024x512x128 capture) x slices",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                      "algorithmic_flops": alg_flops, "kernel_ms": jac_ms},
         "stages_ms": stages,
