@@ -104,7 +104,8 @@ tsvdm_status tsvdm_plan_set_jacobi(tsvdm_plan plan, double tol, int max_sweeps);
  * clusters: clusters launched (slices in flight); stages: row-chunk pipeline depth
  * (2 or 3); ordering: 1 = columns re-ordered by decreasing norm at every sweep
  * (de Rijk), 2 = natural column order; inner_sweeps: Gram sweeps per block pair
- * (1..8).  EINVAL for other values. */
+ * (1..8; default 2: the first over all pairs in a sweep's first round, the others over the
+ * pairs across the two blocks).  EINVAL for other values. */
 tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster_size,
                                    int clusters, int stages, int ordering, int inner_sweeps);
 

@@ -36,7 +36,7 @@ struct tsvdm_plan_s {
   size_t tc_ws_bytes = 0;
   double tol = 0.0;
   int max_sweeps = 40;
-  int width_hint = 0, cluster_hint = 0, grid_hint = 0, stages_hint = 0, inner_sweeps = 1;
+  int width_hint = 0, cluster_hint = 0, grid_hint = 0, stages_hint = 0, inner_sweeps = 2;
   int tol_valid = 0;
   int64_t tol_total = 0;
   void *stage[STG_COUNT] = {};
@@ -495,7 +495,7 @@ tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster
   if (stages != 0 && stages != 2 && stages != 3) return TSVDM_EINVAL;
   if (ordering < 0 || ordering > 2) return TSVDM_EINVAL;
   if (inner_sweeps < 0 || inner_sweeps > 8) return TSVDM_EINVAL;
-  plan->inner_sweeps = inner_sweeps > 0 ? inner_sweeps : 1;
+  plan->inner_sweeps = inner_sweeps > 0 ? inner_sweeps : 2;
   plan->width_hint = block_width;
   plan->stages_hint = stages;
   plan->sort_cols = ordering == 2 ? 0 : 1;

@@ -136,7 +136,7 @@ tsvdm_status run_batch(tsvdm_batch_s *b, const tsvdm_batch_io *io, bool timed) {
   jp.sweeps = b->sweeps;
   jp.rots = b->rots;
   jp.norm2 = nullptr;
-  jp.inner_sweeps = 1;
+  jp.inner_sweeps = 2;
   jp.desc = b->desc;
   if (timed) CKB(cudaEventRecord(b->ev[0], st));
   CKB(jacobi_run<T>(jp, st, b->width, b->cluster, b->clusters, b->stages));

@@ -79,17 +79,43 @@ __device__ __forceinline__ void rr_pair(int n, int round, int q, int &a, int &b)
 template <typename T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
+// Packed upper triangle of a symmetric W2 x W2 matrix: entry (i, j), i <= j.
+template <int W2>
+__device__ __forceinline__ int tri(int i, int j) {
+  if (i > j) {
+    int t = i;
+    i = j;
+    j = t;
+  }
+  return (i * (2 * W2 - i + 1)) / 2 + (j - i);
+}
+
+// The 2 x 2 block of G on rows (pair p) x columns (pair q) after J_p^T B J_q, written
+// with explicit FMAs so that every caller computes bit-identical values.
+template <typename T>
+__device__ __forceinline__ void rot_block(T b00, T b01, T b10, T b11, T c1, T s1, T c2, T s2,
+                                          T &o00, T &o01, T &o10, T &o11) {
+  const T r00 = fma(c1, b00, -(s1 * b10)), r01 = fma(c1, b01, -(s1 * b11));
+  const T r10 = fma(s1, b00, c1 * b10), r11 = fma(s1, b01, c1 * b11);
+  o00 = fma(c2, r00, -(s2 * r01));
+  o01 = fma(s2, r00, c2 * r01);
+  o10 = fma(c2, r10, -(s2 * r11));
+  o11 = fma(s2, r10, c2 * r11);
+}
+
 constexpr int MAXSORT = 1024;        // slices with more columns keep the natural order
 
 template <typename T, int W2, int NS>
 struct Smem {
   T buf[Cfg<T, W2, NS>::BUF];            // streamed chunk / Gram partials
-  T G[W2 * Cfg<T, W2, NS>::LDG];         // Gram matrix
+  T G[2][W2 * (W2 + 1) / 2];         // Gram, packed upper triangle, double-buffered
   T Q[W2 * W2];                      // accumulated rotation, Q(r, j) at Q[j*W2 + r]
-  T cs[W2];                          // c, s per pair of the current step
-  T dd[W2];                          // updated diagonal per pair
-  int pi[W2 / 2], pj[W2 / 2];
-  int rot[W2 / 2];
+  T cs[2][W2];                       // c, s per pair, slot = step parity
+  T dd[2][W2];                       // updated diagonal per pair
+  int pi[2][W2 / 2], pj[2][W2 / 2];
+  int rot[2][W2 / 2];
+  int pos[2][W2];                    // 2 * pair + role of every column in the step
+  int gcur;                          // buffer of G holding the current Gram
   int col[W2];                       // global column of local column c (-1 = padding)
   int any_rot;                       // this block pair rotated
   int step_rot;                      // the last inner sweep rotated
@@ -207,10 +233,12 @@ __device__ void gram(Smem<T, W2, NS> &s, const T *__restrict__ Wsl, int rows, in
   __syncthreads();
   for (int idx = tid; idx < W2 * W2; idx += NT) {
     int i = idx / W2, j = idx % W2;
+    if (i > j) continue;
     T sum = T(0);
     for (int g = 0; g < C::KG; ++g) sum += gp[(g * W2 + i) * W2 + j];
-    s.G[i * C::LDG + j] = sum;
+    s.G[0][tri<W2>(i, j)] = sum;
   }
+  if (tid == 0) s.gcur = 0;
   __syncthreads();
 }
 
@@ -226,22 +254,63 @@ __device__ __forceinline__ void inner_pair(bool full, int step, int k, int &i, i
   }
 }
 
+// Rotation of one pair from its current Gram entries (a = g_ii, b = g_jj, g = g_ij):
+// angle and convergence test in FP64, stored in slot `sl` as pair k.
+template <typename T, int W2, int NS>
+__device__ __forceinline__ void pair_angle(Smem<T, W2, NS> &s, int sl, int k, int i, int j,
+                                           double a, double b, double g, double tol2) {
+  s.pi[sl][k] = i;
+  s.pj[sl][k] = j;
+  s.pos[sl][i] = 2 * k;
+  s.pos[sl][j] = 2 * k + 1;
+  int rot = 0;
+  if (!(isfinite(a) && isfinite(b))) {
+    s.nonfinite = 1;
+  } else if (g * g > tol2 * (a * b)) {
+    // zeta = (b - a) / (2 g);  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
+    //   = sign(zeta) |2g| / (|b - a| + sqrt((b - a)^2 + 4 g^2))   (one sqrt, one divide)
+    const double h = b - a, g2 = 2.0 * g;
+    const double sgn = ((h >= 0.0) == (g2 >= 0.0)) ? 1.0 : -1.0;
+    const double t = sgn * fabs(g2) / (fabs(h) + sqrt(h * h + g2 * g2));
+    const double c = rsqrt(1.0 + t * t);
+    s.cs[sl][2 * k] = (T)c;
+    s.cs[sl][2 * k + 1] = (T)(c * t);
+    s.dd[sl][2 * k] = (T)(a - t * g);
+    s.dd[sl][2 * k + 1] = (T)(b + t * g);
+    rot = 1;
+    s.any_rot = 1;
+    s.step_rot = 1;
+    atomicAdd((unsigned long long *)&s.nrot, 1ull);
+  }
+  if (!rot) {
+    s.cs[sl][2 * k] = T(1);
+    s.cs[sl][2 * k + 1] = T(0);
+  }
+  s.rot[sl][k] = rot;
+}
+
 // One cyclic two-sided Jacobi sweep on G (all pairs when `full`, else only pairs across
-// the two blocks), accumulating the rotations in Q.  Sets s.any_rot.
+// the two blocks), accumulating the rotations in Q.  Sets s.any_rot and s.step_rot.
+//
+// One barrier per step: while warps 0..6 apply step s to the Gram (read from one buffer,
+// written to the other) and to Q, the last warp already computes the angles of step s+1
+// from the Gram before step s and the rotations of step s, with the same 2 x 2
+// arithmetic the update warps use, so both see bit-identical entries.
 template <typename T, int W2, int NS>
 __device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool first) {
-  using C = Cfg<T, W2, NS>;
   const int tid = threadIdx.x;
   constexpr int NP = W2 / 2;
-  // fresh-Gram convergence test: does any pair exceed the threshold?
-  // |g| > tol sqrt(a b)  <=>  g^2 > tol^2 a b   (a, b >= 0; FP64, no square root)
+  constexpr int AW = NT / 32 - 1;          // the angle warp
+  constexpr int NU = NT - 32;              // update threads
   const double tol2 = tol * tol;
+  const int g0 = s.gcur;
+  // fresh-Gram convergence test: |g| > tol sqrt(a b)  <=>  g^2 > tol^2 a b  (FP64)
   int need = 0;
   for (int idx = tid; idx < W2 * W2; idx += NT) {
     int i = idx / W2, j = idx % W2;
-    if (i < j && (full || (i < W2 / 2 && j >= W2 / 2))) {
-      double a = (double)s.G[i * C::LDG + i], b = (double)s.G[j * C::LDG + j];
-      double g = (double)s.G[i * C::LDG + j];
+    if (i < j && (full || (i < NP && j >= NP))) {
+      double a = (double)s.G[g0][tri<W2>(i, i)], b = (double)s.G[g0][tri<W2>(j, j)];
+      double g = (double)s.G[g0][tri<W2>(i, j)];
       if (isfinite(a) && isfinite(b) && g * g > tol2 * (a * b)) need = 1;
     }
   }
@@ -254,81 +323,93 @@ __device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool firs
   if (first) {
     for (int idx = tid; idx < W2 * W2; idx += NT) s.Q[idx] = (idx / W2 == idx % W2) ? T(1) : T(0);
   }
+  const int nsteps = full ? W2 - 1 : NP;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp == AW && lane < NP) {     // angles of step 0 from the fresh Gram
+    int i, j;
+    inner_pair<W2>(full, 0, lane, i, j);
+    pair_angle<T, W2, NS>(s, 0, lane, i, j, (double)s.G[g0][tri<W2>(i, i)],
+                          (double)s.G[g0][tri<W2>(j, j)], (double)s.G[g0][tri<W2>(i, j)], tol2);
+  }
   __syncthreads();
-  const int nsteps = full ? W2 - 1 : W2 / 2;
   for (int step = 0; step < nsteps; ++step) {
-    if (tid < NP) {
-      int i, j;
-      inner_pair<W2>(full, step, tid, i, j);
-      s.pi[tid] = i;
-      s.pj[tid] = j;
-      double a = (double)s.G[i * C::LDG + i];
-      double b = (double)s.G[j * C::LDG + j];
-      double g = (double)s.G[i * C::LDG + j];
-      int rot = 0;
-      if (!(isfinite(a) && isfinite(b))) {
-        s.nonfinite = 1;
-      } else if (g * g > tol2 * (a * b)) {
-        // zeta = (b - a) / (2 g);  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
-        //   = sign(zeta) |2g| / (|b - a| + sqrt((b - a)^2 + 4 g^2))   (one sqrt, one divide)
-        const double h = b - a, g2 = 2.0 * g;
-        const double sgn = ((h >= 0.0) == (g2 >= 0.0)) ? 1.0 : -1.0;
-        const double t = sgn * fabs(g2) / (fabs(h) + sqrt(h * h + g2 * g2));
-        const double c = rsqrt(1.0 + t * t);
-        s.cs[2 * tid] = (T)c;
-        s.cs[2 * tid + 1] = (T)(c * t);
-        s.dd[2 * tid] = (T)(a - t * g);
-        s.dd[2 * tid + 1] = (T)(b + t * g);
-        rot = 1;
-        s.any_rot = 1;
-        s.step_rot = 1;
+    const int sl = step & 1;
+    const T *Gs = s.G[g0 ^ (step & 1)];
+    T *Gd = s.G[g0 ^ ((step + 1) & 1)];
+    if (warp == AW) {
+      if (lane < NP && step + 1 < nsteps) {
+        int i, j;
+        inner_pair<W2>(full, step + 1, lane, i, j);
+        const int pi_ = s.pos[sl][i], pj_ = s.pos[sl][j];
+        const int p = pi_ >> 1, q = pj_ >> 1, ri = pi_ & 1, rj = pj_ & 1;
+        T a = s.rot[sl][p] ? s.dd[sl][pi_] : Gs[tri<W2>(i, i)];
+        T b = s.rot[sl][q] ? s.dd[sl][pj_] : Gs[tri<W2>(j, j)];
+        T g;
+        if (p == q) {
+          g = s.rot[sl][p] ? T(0) : Gs[tri<W2>(i, j)];
+        } else {
+          // the block the update warps form: rows of the lower pair index, columns of the
+          // higher one, so the entry is bit-identical to the one they store
+          const int pl = p < q ? p : q, ph = p < q ? q : p;
+          const int rl = p < q ? ri : rj, rh = p < q ? rj : ri;
+          const int i1 = s.pi[sl][pl], j1 = s.pj[sl][pl], i2 = s.pi[sl][ph], j2 = s.pj[sl][ph];
+          T o[4];
+          rot_block(Gs[tri<W2>(i1, i2)], Gs[tri<W2>(i1, j2)], Gs[tri<W2>(j1, i2)],
+                    Gs[tri<W2>(j1, j2)], s.cs[sl][2 * pl], s.cs[sl][2 * pl + 1], s.cs[sl][2 * ph],
+                    s.cs[sl][2 * ph + 1], o[0], o[1], o[2], o[3]);
+          g = o[2 * rl + rh];
+        }
+        pair_angle<T, W2, NS>(s, sl ^ 1, lane, i, j, (double)a, (double)b, (double)g, tol2);
       }
-      if (!rot) {
-        s.cs[2 * tid] = T(1);
-        s.cs[2 * tid + 1] = T(0);
+    } else {
+      // G_{s+1} = J^T G_s J on the blocks pp <= qq (the rest is their transpose)
+      constexpr int NB = NP * (NP + 1) / 2;
+      for (int blk = tid; blk < NB; blk += NU) {
+        // blk -> (pp, qq), pp <= qq: rows of the packed upper triangle of an NP x NP grid
+        int pp = (int)((2.0f * NP + 1.0f - sqrtf((2.0f * NP + 1.0f) * (2.0f * NP + 1.0f) -
+                                                  8.0f * blk)) * 0.5f);
+        if (pp < 0) pp = 0;
+        while (pp > 0 && pp * (2 * NP - pp + 1) / 2 > blk) --pp;
+        while ((pp + 1) * (2 * NP - pp) / 2 <= blk) ++pp;
+        const int qq = pp + (blk - pp * (2 * NP - pp + 1) / 2);
+        const int i1 = s.pi[sl][pp], j1 = s.pj[sl][pp];
+        if (pp == qq) {
+          if (s.rot[sl][pp]) {
+            Gd[tri<W2>(i1, i1)] = s.dd[sl][2 * pp];
+            Gd[tri<W2>(j1, j1)] = s.dd[sl][2 * pp + 1];
+            Gd[tri<W2>(i1, j1)] = T(0);
+          } else {
+            Gd[tri<W2>(i1, i1)] = Gs[tri<W2>(i1, i1)];
+            Gd[tri<W2>(j1, j1)] = Gs[tri<W2>(j1, j1)];
+            Gd[tri<W2>(i1, j1)] = Gs[tri<W2>(i1, j1)];
+          }
+          continue;
+        }
+        const int i2 = s.pi[sl][qq], j2 = s.pj[sl][qq];
+        T o00, o01, o10, o11;
+        rot_block(Gs[tri<W2>(i1, i2)], Gs[tri<W2>(i1, j2)], Gs[tri<W2>(j1, i2)],
+                  Gs[tri<W2>(j1, j2)], s.cs[sl][2 * pp], s.cs[sl][2 * pp + 1],
+                  s.cs[sl][2 * qq], s.cs[sl][2 * qq + 1], o00, o01, o10, o11);
+        Gd[tri<W2>(i1, i2)] = o00;
+        Gd[tri<W2>(i1, j2)] = o01;
+        Gd[tri<W2>(j1, i2)] = o10;
+        Gd[tri<W2>(j1, j2)] = o11;
       }
-      s.rot[tid] = rot;
-    }
-    __syncthreads();
-    // G <- J^T G J, block by block (blocks of this step's pairs partition G)
-    for (int blk = tid; blk < NP * NP; blk += NT) {
-      int pp = blk / NP, qq = blk % NP;
-      int rp = s.rot[pp], rq = s.rot[qq];
-      if (!(rp | rq)) continue;
-      int i1 = s.pi[pp], j1 = s.pj[pp], i2 = s.pi[qq], j2 = s.pj[qq];
-      if (pp == qq) {
-        s.G[i1 * C::LDG + i1] = s.dd[2 * pp];
-        s.G[j1 * C::LDG + j1] = s.dd[2 * pp + 1];
-        s.G[i1 * C::LDG + j1] = T(0);
-        s.G[j1 * C::LDG + i1] = T(0);
-        continue;
+      // Q <- Q J
+      for (int it = tid; it < W2 * NP; it += NU) {
+        int qq = it / W2, r = it % W2;
+        if (!s.rot[sl][qq]) continue;
+        int i = s.pi[sl][qq], j = s.pj[sl][qq];
+        T c = s.cs[sl][2 * qq], sn = s.cs[sl][2 * qq + 1];
+        T x = s.Q[i * W2 + r], y = s.Q[j * W2 + r];
+        s.Q[i * W2 + r] = c * x - sn * y;
+        s.Q[j * W2 + r] = sn * x + c * y;
       }
-      T c1 = s.cs[2 * pp], s1 = s.cs[2 * pp + 1];
-      T c2 = s.cs[2 * qq], s2 = s.cs[2 * qq + 1];
-      T b00 = s.G[i1 * C::LDG + i2], b01 = s.G[i1 * C::LDG + j2];
-      T b10 = s.G[j1 * C::LDG + i2], b11 = s.G[j1 * C::LDG + j2];
-      // rows (J_p^T)
-      T r00 = c1 * b00 - s1 * b10, r01 = c1 * b01 - s1 * b11;
-      T r10 = s1 * b00 + c1 * b10, r11 = s1 * b01 + c1 * b11;
-      // columns (J_q)
-      s.G[i1 * C::LDG + i2] = c2 * r00 - s2 * r01;
-      s.G[i1 * C::LDG + j2] = s2 * r00 + c2 * r01;
-      s.G[j1 * C::LDG + i2] = c2 * r10 - s2 * r11;
-      s.G[j1 * C::LDG + j2] = s2 * r10 + c2 * r11;
     }
-    // Q <- Q J
-    for (int it = tid; it < W2 * NP; it += NT) {
-      int qq = it / W2, r = it % W2;
-      if (!s.rot[qq]) continue;
-      int i = s.pi[qq], j = s.pj[qq];
-      T c = s.cs[2 * qq], sn = s.cs[2 * qq + 1];
-      T x = s.Q[i * W2 + r], y = s.Q[j * W2 + r];
-      s.Q[i * W2 + r] = c * x - sn * y;
-      s.Q[j * W2 + r] = sn * x + c * y;
-    }
-    if (tid < NP && s.rot[tid]) atomicAdd((unsigned long long *)&s.nrot, 1ull);
     __syncthreads();
   }
+  if (tid == 0) s.gcur = g0 ^ (nsteps & 1);
+  __syncthreads();
 }
 
 // [Wsl(:, col)] <- [Wsl(:, col)] Q, rows streamed through the cp.async pipeline; results
@@ -482,12 +563,12 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
           __syncthreads();
           gram<T, W2, NS>(s, Wsl, rows, rows);
           for (int is = 0; is < p.inner_sweeps; ++is) {
-            inner_sweep<T, W2, NS>(s, tol, round == 0 || is > 0, is == 0);
+            inner_sweep<T, W2, NS>(s, tol, round == 0, is == 0);
             if (!s.step_rot) break;
           }
           __syncthreads();
           if (sorted && tid < W2 && s.col[tid] >= 0)     // squared norms after this step
-            __stcg(nrm2 + s.col[tid], (float)s.G[tid * C::LDG + tid]);
+            __stcg(nrm2 + s.col[tid], (float)s.G[s.gcur][tri<W2>(tid, tid)]);
           if (s.any_rot) {
             if (tid == 0) s.sweep_any = 1;
             apply_q<T, W2, NS>(s, Wsl, rows, rows);
