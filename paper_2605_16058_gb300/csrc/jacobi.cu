@@ -51,7 +51,6 @@ struct Cfg {
   static constexpr int KG = NT / TILES;               // Gram K-groups
   static constexpr int CPW = W2 / 8;                  // apply: columns per warp
   static constexpr int RPT = RC / 32;                 // apply: rows per thread
-  static constexpr int LDG = W2 + 1;                  // Gram stride
   static constexpr int CHUNK = W2 * LDR;
   static constexpr int GPART = KG * W2 * W2;
   static constexpr int BUF = NS * CHUNK > GPART ? NS * CHUNK : GPART;
