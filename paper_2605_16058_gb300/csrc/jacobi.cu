@@ -108,7 +108,7 @@ template <typename T, int W2, int NS>
 struct Smem {
   T buf[Cfg<T, W2, NS>::BUF];            // streamed chunk / Gram partials
   T G[2][W2 * (W2 + 1) / 2];         // Gram, packed upper triangle, double-buffered
-  T Q[W2 * W2];                      // accumulated rotation, Q(r, j) at Q[j*W2 + r]
+  __align__(16) T Q[W2 * W2];        // accumulated rotation, Q(r, j) at Q[r*W2 + j]
   T cs[2][W2];                       // c, s per pair, slot = step parity
   T dd[2][W2];                       // updated diagonal per pair
   int pi[2][W2 / 2], pj[2][W2 / 2];
@@ -253,6 +253,23 @@ __device__ __forceinline__ void inner_pair(bool full, int step, int k, int &i, i
   }
 }
 
+// Convergence test |g| > tol sqrt(a b)  <=>  g^2 > tol^2 a b (a, b >= 0), decided in FP64.
+// maybe_rotate is a conservative single-precision filter in front of it: it can only
+// reject pairs that are at least 2% below the threshold (single-precision products carry
+// relative errors ~1e-7), and defers to FP64 whenever a product over- or underflows.
+template <typename T>
+__device__ __forceinline__ bool maybe_rotate(T a, T b, T g, double tol2) {
+  const float af = (float)a, bf = (float)b, gf = (float)g;
+  const float lhs = gf * gf, rhs = (float)tol2 * (af * bf);
+  if (!(lhs < 1e30f && rhs < 1e30f) || (rhs < 1e-30f && af != 0.f && bf != 0.f)) return true;
+  return lhs > 0.98f * rhs;
+}
+template <typename T>
+__device__ __forceinline__ bool exceeds(T a, T b, T g, double tol2) {
+  const double ad = (double)a, bd = (double)b, gd = (double)g;
+  return isfinite(ad) && isfinite(bd) && gd * gd > tol2 * (ad * bd);
+}
+
 // Rotation of one pair from its current Gram entries (a = g_ii, b = g_jj, g = g_ij):
 // angle and convergence test in FP64, stored in slot `sl` as pair k.
 template <typename T, int W2, int NS>
@@ -265,7 +282,7 @@ __device__ __forceinline__ void pair_angle(Smem<T, W2, NS> &s, int sl, int k, in
   int rot = 0;
   if (!(isfinite(a) && isfinite(b))) {
     s.nonfinite = 1;
-  } else if (g * g > tol2 * (a * b)) {
+  } else if (maybe_rotate((T)a, (T)b, (T)g, tol2) && g * g > tol2 * (a * b)) {
     // zeta = (b - a) / (2 g);  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
     //   = sign(zeta) |2g| / (|b - a| + sqrt((b - a)^2 + 4 g^2))   (one sqrt, one divide)
     const double h = b - a, g2 = 2.0 * g;
@@ -308,9 +325,8 @@ __device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool firs
   for (int idx = tid; idx < W2 * W2; idx += NT) {
     int i = idx / W2, j = idx % W2;
     if (i < j && (full || (i < NP && j >= NP))) {
-      double a = (double)s.G[g0][tri<W2>(i, i)], b = (double)s.G[g0][tri<W2>(j, j)];
-      double g = (double)s.G[g0][tri<W2>(i, j)];
-      if (isfinite(a) && isfinite(b) && g * g > tol2 * (a * b)) need = 1;
+      const T a = s.G[g0][tri<W2>(i, i)], b = s.G[g0][tri<W2>(j, j)], g = s.G[g0][tri<W2>(i, j)];
+      if (maybe_rotate(a, b, g, tol2) && exceeds(a, b, g, tol2)) need = 1;
     }
   }
   __syncthreads();                   // every thread has read step_rot of the previous call
@@ -394,15 +410,15 @@ __device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool firs
         Gd[tri<W2>(j1, i2)] = o10;
         Gd[tri<W2>(j1, j2)] = o11;
       }
-      // Q <- Q J
+      // Q <- Q J  (lanes walk the pairs of one row: distinct columns of that row)
       for (int it = tid; it < W2 * NP; it += NU) {
-        int qq = it / W2, r = it % W2;
+        int r = it / NP, qq = it % NP;
         if (!s.rot[sl][qq]) continue;
         int i = s.pi[sl][qq], j = s.pj[sl][qq];
         T c = s.cs[sl][2 * qq], sn = s.cs[sl][2 * qq + 1];
-        T x = s.Q[i * W2 + r], y = s.Q[j * W2 + r];
-        s.Q[i * W2 + r] = c * x - sn * y;
-        s.Q[j * W2 + r] = sn * x + c * y;
+        T x = s.Q[r * W2 + i], y = s.Q[r * W2 + j];
+        s.Q[r * W2 + i] = c * x - sn * y;
+        s.Q[r * W2 + j] = sn * x + c * y;
       }
     }
     __syncthreads();
@@ -443,9 +459,20 @@ __device__ void apply_q(Smem<T, W2, NS> &s, T *__restrict__ Wsl, int rows, int l
       for (int e = 0; e < C::CPW; ++e) acc[q][e] = T(0);
 #pragma unroll 4
     for (int c = 0; c < W2; ++c) {
-      T qv[C::CPW];
+      T qv[C::CPW];                   // Q(c, j0 .. j0+CPW-1): contiguous, 16-byte loads
+      if constexpr ((C::CPW * sizeof(T)) % 16 == 0) {
+        using V = typename Vec16<T>::type;
 #pragma unroll
-      for (int e = 0; e < C::CPW; ++e) qv[e] = s.Q[(j0 + e) * W2 + c];
+        for (int e = 0; e < C::CPW; e += C::VN) {
+          V v = *reinterpret_cast<const V *>(&s.Q[c * W2 + j0 + e]);
+          const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+          for (int u = 0; u < C::VN; ++u) qv[e + u] = pv[u];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < C::CPW; ++e) qv[e] = s.Q[c * W2 + j0 + e];
+      }
 #pragma unroll
       for (int q = 0; q < C::RPT; ++q) {
         T a = ch[c * C::LDR + lane + 32 * q];
