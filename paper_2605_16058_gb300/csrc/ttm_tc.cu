@@ -29,14 +29,16 @@ namespace {
 
 constexpr int TBM = 128;
 constexpr int TBK = 32;
-constexpr int STAGES = 2;
+constexpr int MAX_STAGES = 4;
 constexpr int TC_THREADS = 256;
 constexpr unsigned SPIN_LIMIT = 1u << 26;
 
 struct TcParams {
   int64_t P, n, J;
   int npad;          // J rounded up to 16 (J <= 256) or to 128 (J <= 512)
-  int box_rows;      // rows of one B tensor-map box (divides npad, <= 256)
+  int nsub;          // output columns of one CTA (npad); blockIdx.x picks the column group
+  int box_rows;      // rows of one B tensor-map box (divides nsub, <= 256)
+  int stages;        // pipeline depth (2..MAX_STAGES)
   int kt_count;      // ceil(n / TBK)
   int prec;          // TSVDM_P_BF16X3 or TSVDM_P_TF32
   float *Y;
@@ -131,7 +133,7 @@ struct TcLayout {
   uint32_t a_bytes, b_bytes;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int npad, int prec) {
+__host__ __device__ inline TcLayout tc_layout(int npad, int prec, int stages) {
   TcLayout L;
   const uint32_t raw = TBK * TBM * 4;                       // 16 KB
   const uint32_t a = (prec == TSVDM_P_BF16X3) ? 2u * TBM * 64 : TBM * 128u;   // 16 KB
@@ -144,7 +146,7 @@ __host__ __device__ inline TcLayout tc_layout(int npad, int prec) {
   uint32_t st = raw + a + b;
   st = (st + 1023) & ~1023u;
   L.stage = st;
-  L.total = STAGES * st + 1024;                            // + barriers / TMEM address
+  L.total = stages * st + 1024;                            // + barriers / TMEM address
   return L;
 }
 
@@ -154,16 +156,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // align the dynamic shared memory base to 1024 bytes
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const TcLayout L = tc_layout(p.npad, p.prec);
+  const int STAGES = p.stages;
+  const TcLayout L = tc_layout(p.nsub, p.prec, STAGES);
   uint64_t *full = (uint64_t *)(smem + STAGES * L.stage);
-  uint64_t *conv = full + STAGES;
-  uint64_t *empty = conv + STAGES;
-  uint64_t *done = empty + STAGES;
+  uint64_t *conv = full + MAX_STAGES;
+  uint64_t *empty = conv + MAX_STAGES;
+  uint64_t *done = empty + MAX_STAGES;
   uint32_t *tmem_slot = (uint32_t *)(done + 1);
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * TBM;
+  // the halves of one row tile are adjacent blocks, so the second reads X from L2
+  const int64_t m0 = (int64_t)blockIdx.y * TBM;
+  const int n_base = blockIdx.x * p.nsub;          // first output column of this CTA
   const bool bf = p.prec == TSVDM_P_BF16X3;
   const int nk = p.kt_count;
 
@@ -202,9 +207,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int ops = bf ? 2 : 1;
       const uint32_t row_bytes = bf ? 64 : 128;
       for (int o = 0; o < ops; ++o)
-        for (int r0 = 0; r0 < p.npad; r0 += p.box_rows)
-          tma_load_2d(st + L.b + (uint32_t)o * p.npad * row_bytes + (uint32_t)r0 * row_bytes,
-                      &mapB, &full[s], kt * TBK, o * p.npad + r0);
+        for (int r0 = 0; r0 < p.nsub; r0 += p.box_rows)
+          tma_load_2d(st + L.b + (uint32_t)o * p.nsub * row_bytes + (uint32_t)r0 * row_bytes,
+                      &mapB, &full[s], kt * TBK, o * p.npad + n_base + r0);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -220,8 +225,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       unsigned char *st = smem + s * L.stage;
       for (int kk = 0; kk < ksub; ++kk) {
         const uint32_t koff = kk * 32;                      // 32 bytes per k-step
-        for (int n0 = 0; n0 < p.npad; n0 += 256) {
-          const uint32_t nn = (p.npad - n0) < 256 ? (uint32_t)(p.npad - n0) : 256u;
+        for (int n0 = 0; n0 < p.nsub; n0 += 256) {
+          const uint32_t nn = (p.nsub - n0) < 256 ? (uint32_t)(p.nsub - n0) : 256u;
           const uint32_t idesc = instr_desc(fmt, nn);
           const uint32_t d = tmem + (uint32_t)n0;
           const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint64_t ahi = smem_desc(st + L.a + koff, sbo, lay);
             uint64_t alo = smem_desc(st + L.a + TBM * 64 + koff, sbo, lay);
             uint64_t bhi = smem_desc(st + L.b + n0 * row_bytes + koff, sbo, lay);
-            uint64_t blo = smem_desc(st + L.b + (uint32_t)p.npad * row_bytes + n0 * row_bytes + koff,
+            uint64_t blo = smem_desc(st + L.b + (uint32_t)p.nsub * row_bytes + n0 * row_bytes + koff,
                                      sbo, lay);
             mma_f16(d, ahi, bhi, idesc, acc);
             mma_f16(d, ahi, blo, idesc, 1u);
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const float beta = p.beta_ptr ? (float)(*p.beta_ptr) : 0.f;
     const int64_t grow = m0 + row;
     const uint32_t lane_base = (uint32_t)(32 * (warp - 4)) << 16;
-    for (int j0 = 0; j0 < p.npad; j0 += 16) {
+    for (int j0 = 0; j0 < p.nsub; j0 += 16) {
       uint32_t v[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (ok && grow < p.P) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const int64_t col = j0 + e;
+          const int64_t col = n_base + j0 + e;
           if (col < p.J) {
             float y = scale * __uint_as_float(v[e]);
             if (p.Z) y = fmaf(beta, p.Z[grow + p.P * col], y);
@@ -401,6 +406,10 @@ cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t
   if (prec != TSVDM_P_BF16X3 && prec != TSVDM_P_TF32) return cudaErrorInvalidValue;
   const int npad = tc_npad(J);
   const int kpad = (int)((n + TBK - 1) / TBK * TBK);
+  // One CTA owns all J outputs of its row tile (measured faster than splitting J over two
+  // CTAs, which re-converts X and halves the MMA work per stage).
+  const int nsplit = 1;
+  const int nsub = npad;
   const int box_rows = npad <= 256 ? npad : 128;
   if (ws_bytes < ttm_tc_workspace(n, J)) return cudaErrorInvalidValue;
   void *Bk = (void *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
@@ -441,6 +450,7 @@ cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t
   p.n = n;
   p.J = J;
   p.npad = npad;
+  p.nsub = nsub;
   p.box_rows = box_rows;
   p.kt_count = kpad / TBK;
   p.prec = prec;
@@ -451,14 +461,21 @@ cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t
   p.sumsq = sumsq;
   p.status = status;
   uint32_t cols = 32;
-  while (cols < (uint32_t)npad) cols <<= 1;
+  while (cols < (uint32_t)nsub) cols <<= 1;
   p.tmem_cols = cols;
-  const TcLayout L = tc_layout(npad, prec);
+  // two CTAs per SM with two stages when they fit, else the deepest pipeline that fits
+  int stages = 2;
+  if (2 * (tc_layout(nsub, prec, 2).total + 1024) > 227 * 1024) {
+    stages = MAX_STAGES;
+    while (stages > 2 && tc_layout(nsub, prec, stages).total + 1024 > 227 * 1024) --stages;
+  }
+  p.stages = stages;
+  const TcLayout L = tc_layout(nsub, prec, stages);
   const size_t smem = L.total + 1024;
   cudaError_t e = cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((P + TBM - 1) / TBM);
+  const dim3 grid((unsigned)nsplit, (unsigned)((P + TBM - 1) / TBM));
   ttm_tc_kernel<<<grid, TC_THREADS, smem, st>>>(mapX, mapB, p);
   return cudaGetLastError();
 }
