@@ -47,6 +47,8 @@ WORKLOADS = {
     "batch": (None, None, "64 uneven tensors, t-SVDM-I k=16 / t-SVDM-II eps=1e-3, Haar M, "
                           "one CUDA-graph batch"),
     "batch-small": (None, None, "8 uneven tensors (first 8 of the 64-tensor batch), graph"),
+    # the mode-3 TTM alone (component benchmark of the transform, tensor cores)
+    "ttm": ((1024, 512, 365), None, "mode-3 TTM alone, 1024x512x365 FP32 X, 365x365 M"),
 }
 FP32_LANES_PER_SM = 128
 SMS = 152
@@ -265,6 +267,47 @@ def run_batch_bench(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_ttm_bench(args, local):
+    """The forward mode-3 TTM alone: input GB/s of Y = X x_3 M in the chosen precision,
+    with its HBM roofline (2 P n + n^2 elements moved) and, for BF16x3, tensor work."""
+    import numpy as np
+    import torch
+    from paper_2605_16058_gb300 import build, synth
+    from paper_2605_16058_gb300.tsvdm import Plan
+    build.build()
+    torch.cuda.set_device(local)
+    (n1, n2, n3), _, desc = WORKLOADS["ttm"]
+    g = torch.Generator(device="cuda").manual_seed(7)
+    X = torch.randn(n3, n2, n1, device="cuda", generator=g)
+    M = torch.from_numpy(synth.haar_orthogonal(n3, np.random.default_rng(7))
+                         .astype(np.float32)).cuda()
+    Y = torch.empty_like(X)
+    plan = Plan(n1, n2, n3, dtype=torch.float32, prec=args.prec)
+    for _ in range(max(3, args.warmup)):
+        plan.transform(X, M, out=Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.transform(X, M, out=Y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    P = n1 * n2
+    byts = (2 * P * n3 + n3 * n3) * 4
+    pk, src = peaks()
+    gbs = byts / (ms * 1e-3) / 1e9
+    line = {"metric": "mode-3 TTM input GB/s", "value": P * n3 * 4 / (ms * 1e-3) / 1e9,
+            "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+            "ttm_precision": args.prec, "data": "synthetic",
+            "config": {"workload": desc},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / pk["hbm_gbs"], "peak_source": "of " + src}}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def run_reference(args, wl):
     import numpy as np
     import oracle
@@ -311,6 +354,9 @@ def main():
         return
     if args.workload.startswith("batch"):
         run_batch_bench(args, world, rank, local)
+        return
+    if args.workload == "ttm":
+        run_ttm_bench(args, local)
         return
 
     import numpy as np

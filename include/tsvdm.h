@@ -63,7 +63,8 @@ typedef enum {
 typedef enum { TSVDM_F32 = 0, TSVDM_F64 = 1 } tsvdm_dtype;
 
 /* Arithmetic of the mode-3 TTMs.  The slice SVDs run in the storage precision (FP32
- * data with FP64 rotation angles and convergence test for F32; FP64 for F64).
+ * data, angles and convergence test for F32; FP64 for F64); see tsvdm_plan_set_engine
+ * for the engine of their dense products.
  *   TSVDM_P_FP64    FP64 CUDA-core products (dtype F64 only)
  *   TSVDM_P_FP32    FP32 CUDA-core products (dtype F32)
  *   TSVDM_P_TF32    one TF32 tensor-core product, FP32 accumulation (dtype F32)
@@ -108,6 +109,29 @@ tsvdm_status tsvdm_plan_set_jacobi(tsvdm_plan plan, double tol, int max_sweeps);
  * pairs across the two blocks).  EINVAL for other values. */
 tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster_size,
                                    int clusters, int stages, int ordering, int inner_sweeps);
+
+/* Engine of the dense products inside the slice SVDs (the block Gram G = W^T W and the
+ * rotation apply W <- W Q of every block pair of the one-sided Jacobi, Sec. 3.2's
+ * per-slice svd):
+ *   TSVDM_JACOBI_AUTO  tensor cores for F32 plans, FMA for F64 (default; see below)
+ *   TSVDM_JACOBI_FMA   FP32 / FP64 FMA on the CUDA cores
+ *   TSVDM_JACOBI_TC    tcgen05 tensor cores (F32 only).  Gram: every element split as
+ *                      x = h + l, h = tf32(x), l = tf32(x - h), G = H^T H + L^T H + H^T L.
+ *                      Apply: W + W (Q - I) with W and Q - I split into three BF16 terms
+ *                      (x1 + x2 + x3, residual <= 2^-27 |x|) and the six products of order
+ *                      >= 2^-24.  FP32 accumulation.  Block pairs are 64 columns.
+ *                      One persistent CTA per SM of three 256-thread workers; under
+ *                      tsvdm_plan_set_tuning, cluster_size is the number of workers that
+ *                      share a slice (1 or 3; 0 = 1 when there are at least two slices per
+ *                      SM, else 3), clusters the CTAs launched, stages is ignored.
+ * AUTO uses TC for F32 slices of at least 64 columns unless block_width asks for 16 or 32.
+ * ENOTSUP for TC on an F64 plan, EINVAL for other values. */
+typedef enum {
+  TSVDM_JACOBI_AUTO = 0,
+  TSVDM_JACOBI_FMA = 1,
+  TSVDM_JACOBI_TC = 2
+} tsvdm_jacobi_engine;
+tsvdm_status tsvdm_plan_set_engine(tsvdm_plan plan, int engine);
 
 /* Y = X x_3 M (inverse = 0) or Y = X x_3 M^{-1} (inverse = 1), Sec. 2.1.  For
  * inverse = 1 on an orthogonal plan, M is the forward matrix and M^T / c^2 is applied;
@@ -266,9 +290,13 @@ tsvdm_status tsvdm_batch_run(tsvdm_batch b, const tsvdm_batch_io *io);
 tsvdm_status tsvdm_batch_capture(tsvdm_batch b, const tsvdm_batch_io *io);
 /* Replays the captured graph on the batch's stream. */
 tsvdm_status tsvdm_batch_launch(tsvdm_batch b);
-/* Autotuner: times the Jacobi launch for each candidate (block width 32/64, cluster size
- * 1/2/4, pipeline stages 2/3) on these inputs and keeps the fastest; choice (nullable,
- * int[4]) receives width, cluster size, stages and the best time in microseconds. */
+/* Autotuner: times the Jacobi launch for each candidate (F32 batches whose slices all
+ * have >= 64 columns: the tensor-core engine with 1 or 3 worker groups per slice; and the
+ * FMA engine with block width 32/64, cluster size 1/2/4, pipeline stages 2/3) on these
+ * inputs and keeps the fastest; choice (nullable, int[4]) receives width, cluster size
+ * (groups per slice for the tensor-core engine), stages (0 = the tensor-core engine) and
+ * the best time in microseconds.  Until tuned, a batch uses TSVDM_JACOBI_AUTO
+ * (tsvdm_plan_set_engine). */
 tsvdm_status tsvdm_batch_tune(tsvdm_batch b, const tsvdm_batch_io *io, int *choice);
 /* Synchronises; sweeps and rotations summed over all slices of the last run, and the
  * device-detected status (ENOCONV, ENONFINITE, ETIMEOUT or OK, then cleared). */

@@ -37,6 +37,7 @@ struct tsvdm_plan_s {
   double tol = 0.0;
   int max_sweeps = 40;
   int width_hint = 0, cluster_hint = 0, grid_hint = 0, stages_hint = 0, inner_sweeps = 2;
+  int engine = JACOBI_AUTO;
   int tol_valid = 0;
   int64_t tol_total = 0;
   void *stage[STG_COUNT] = {};
@@ -195,6 +196,7 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   jp.norm2 = p->sort_cols ? p->norm2 : nullptr;
   jp.inner_sweeps = p->inner_sweeps;
   jp.desc = nullptr;
+  jp.engine = p->engine;
   stage_begin(p, TSVDM_STAGE_JACOBI);
   CK(jacobi_run<T>(jp, p->st, p->width_hint, p->cluster_hint, p->grid_hint, p->stages_hint));
   stage_end(p, TSVDM_STAGE_JACOBI, 1);
@@ -501,6 +503,16 @@ tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster
   plan->sort_cols = ordering == 2 ? 0 : 1;
   plan->cluster_hint = cluster_size;
   plan->grid_hint = clusters;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_set_engine(tsvdm_plan plan, int engine) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  if (engine != TSVDM_JACOBI_AUTO && engine != TSVDM_JACOBI_FMA && engine != TSVDM_JACOBI_TC)
+    return TSVDM_EINVAL;
+  if (engine == TSVDM_JACOBI_TC && plan->dtype != TSVDM_F32) return TSVDM_ENOTSUP;
+  plan->engine = engine == TSVDM_JACOBI_TC ? JACOBI_TC
+                                           : (engine == TSVDM_JACOBI_FMA ? JACOBI_FMA : JACOBI_AUTO);
   return TSVDM_OK;
 }
 

@@ -85,7 +85,7 @@ struct tsvdm_batch_s {
   long long *rots = nullptr;
   std::vector<RelErrArg> h_rel;
   // Jacobi launch shape (autotuned)
-  int width = 0, cluster = 2, clusters = 0, stages = 0;
+  int width = 0, cluster = 2, clusters = 0, stages = 0, engine = JACOBI_AUTO;
   double tol = 0.0;
   int max_sweeps = 40;
   // graph
@@ -138,6 +138,7 @@ tsvdm_status run_batch(tsvdm_batch_s *b, const tsvdm_batch_io *io, bool timed) {
   jp.norm2 = nullptr;
   jp.inner_sweeps = 2;
   jp.desc = b->desc;
+  jp.engine = b->engine;
   if (timed) CKB(cudaEventRecord(b->ev[0], st));
   CKB(jacobi_run<T>(jp, st, b->width, b->cluster, b->clusters, b->stages));
   if (timed) CKB(cudaEventRecord(b->ev[1], st));
@@ -432,24 +433,27 @@ tsvdm_status tsvdm_batch_status(tsvdm_batch b, int64_t *sweeps, int64_t *rotatio
 
 tsvdm_status tsvdm_batch_tune(tsvdm_batch b, const tsvdm_batch_io *io, int *choice) {
   if (!b || !io) return TSVDM_EINVAL;
-  struct Cand { int width, cluster, stages; };
+  struct Cand { int width, cluster, stages, engine; };
   std::vector<Cand> cands;
   const int widths[2] = {32, 64};
   const int clusters[3] = {1, 2, 4};
   const int stages[2] = {2, 3};
+  if (b->dtype == TSVDM_F32 && b->min_cols >= 64)     // tensor-core Gram / apply
+    for (int gps : {1, 3}) cands.push_back({64, gps, 0, JACOBI_TC});
   for (int w : widths) {
     if (w == 64 && b->min_cols < 64) continue;
     for (int c : clusters)
-      for (int s : stages) cands.push_back({w, c, s});
+      for (int s : stages) cands.push_back({w, c, s, JACOBI_FMA});
   }
   tsvdm_status s0 = upload_rel_targets(b, io, false);
   if (s0 != TSVDM_OK) return s0;
   float best = 1e30f;
-  Cand bc = {b->width, b->cluster, b->stages};
+  Cand bc = {b->width, b->cluster, b->stages, b->engine};
   for (const Cand &c : cands) {
     b->width = c.width;
     b->cluster = c.cluster;
     b->stages = c.stages;
+    b->engine = c.engine;
     b->clusters = 0;
     tsvdm_status s = run_any(b, io, true);
     if (s != TSVDM_OK) return s;
@@ -464,11 +468,12 @@ tsvdm_status tsvdm_batch_tune(tsvdm_batch b, const tsvdm_batch_io *io, int *choi
   b->width = bc.width;
   b->cluster = bc.cluster;
   b->stages = bc.stages;
+  b->engine = bc.engine;
   b->last_jacobi_ms = best;
   if (choice) {
     choice[0] = bc.width;
     choice[1] = bc.cluster;
-    choice[2] = bc.stages == 0 ? 2 : bc.stages;
+    choice[2] = bc.engine == JACOBI_TC ? 0 : (bc.stages == 0 ? 2 : bc.stages);
     choice[3] = (int)(best * 1000.f);
   }
   return TSVDM_OK;

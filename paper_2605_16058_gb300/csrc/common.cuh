@@ -79,7 +79,9 @@ struct JacobiParams {
   float *norm2;        // [nslices * cols] squared column norms (nullptr: natural order)
   int inner_sweeps;    // Gram sweeps per block pair (>= 1)
   const SliceDesc *desc; // per-slice matrices (batched), or nullptr (uniform, A/V/sA/sV)
+  int engine;          // JACOBI_AUTO / JACOBI_FMA / JACOBI_TC (Gram and apply products)
 };
+enum { JACOBI_AUTO = 0, JACOBI_FMA = 1, JACOBI_TC = 2 };
 
 template <typename T>
 cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, int cluster_hint,

@@ -8,8 +8,8 @@
 //   1. G = [W_I W_J]^T [W_I W_J]   (W2 x W2 Gram, FP32 (or FP64) FMA, rows streamed
 //      through shared memory in chunks);
 //   2. if some |g_ij| > tol sqrt(g_ii g_jj): one cyclic sweep of two-sided Jacobi on G
-//      (round-robin over all W2 (W2-1)/2 pairs, rotation angle and convergence test in
-//      FP64, G and the accumulated rotation Q updated in the storage precision);
+//      (round-robin over all W2 (W2-1)/2 pairs; rotation angle, convergence test, G and
+//      the accumulated rotation Q in the storage precision);
 //   3. [W_I W_J] <- [W_I W_J] Q and [V_I V_J] <- [V_I V_J] Q.
 // A column pair is rotated exactly as in the scalar method: zeta = (b - a) / (2 g),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t,
@@ -25,8 +25,10 @@
 // between rounds.  Clusters are persistent and pull slice indices from an atomic
 // counter.  Every loop is bounded (sweep cap), and no device code traps.
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -125,6 +127,69 @@ struct Smem {
   int vote[2];
   int ord[MAXSORT];                  // column order of the current sweep
 };
+
+// Barrier of the threads that work on one block pair: the whole CTA (FMA kernel), or one
+// 256-thread group of the tensor-core kernel (named barrier 1 + group).
+struct CtaBar {
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ int sync_or(int v) const { return __syncthreads_or(v); }
+};
+struct GroupBar {
+  int id;
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NT) : "memory");
+  }
+  __device__ __forceinline__ int sync_or(int v) const {
+    int r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
+        " selp.s32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(v), "r"(id), "n"(NT)
+        : "memory");
+    return r;
+  }
+};
+
+// Shared memory of the tensor-core variant (FP32 slices, block pairs of 64 columns).  The
+// member names match Smem, so the inner Gram sweep is shared.  3 CTAs fit on an SM.
+struct SmemTc {
+  static constexpr int W2 = 64;
+  // operand tiles (Gram: two 16 KB [128 x 32] TF32 tiles; apply: the hi and lo
+  // [128 x 32] tiles of one K-block), then the Gram epilogue scratch and the sort keys
+  __align__(1024) unsigned char op[32768];
+  union {
+    struct {
+      float G[2][W2 * (W2 + 1) / 2];       // Gram, packed upper triangle, double-buffered
+      __align__(16) float Q[W2 * W2];      // accumulated rotation, Q(r, j) at Q[r*W2 + j]
+    };
+    // the apply's B operand, (Q - I) split into TF32 hi (first 16 KB) and lo, each two
+    // K-blocks of [64 output columns x 32 K] (G and Q are dead while it lives)
+    __align__(1024) unsigned char bq[32768];
+  };
+  float cs[2][W2];
+  float dd[2][W2];
+  int pi[2][W2 / 2], pj[2][W2 / 2];
+  int rot[2][W2 / 2];
+  int pos[2][W2];
+  int gcur;
+  int col[W2];
+  int any_rot;
+  int step_rot;
+  int sweep_any;
+  int nonfinite;
+  long long nrot;
+  int slice[2];
+  int vote[2];
+  int ord[MAXSORT];
+  uint64_t bar[3];                         // MMA completion: Gram tiles 0 and 1, apply
+  uint32_t tmem;                           // TMEM base (64 FP32 columns x 128 lanes)
+  int fail;                                // a bounded wait ran out
+};
+
+template <typename SM>
+__device__ __forceinline__ float *sort_keys(SM &s) { return reinterpret_cast<float *>(s.buf); }
+__device__ __forceinline__ float *sort_keys(SmemTc &s) { return reinterpret_cast<float *>(s.op); }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -270,11 +335,33 @@ __device__ __forceinline__ bool exceeds(T a, T b, T g, double tol2) {
   return isfinite(ad) && isfinite(bd) && gd * gd > tol2 * (ad * bd);
 }
 
-// Rotation of one pair from its current Gram entries (a = g_ii, b = g_jj, g = g_ij):
-// angle and convergence test in FP64, stored in slot `sl` as pair k.
-template <typename T, int W2, int NS>
-__device__ __forceinline__ void pair_angle(Smem<T, W2, NS> &s, int sl, int k, int i, int j,
-                                           double a, double b, double g, double tol2) {
+// Single-precision form of the test for FP32 slices (the threshold tol ~ 4 sqrt(m) 2^-24
+// is itself a rounding-level quantity, so deciding it in FP32 moves it by ~1e-7
+// relative): g^2 > tol^2 a b while the products stay in the normal range, else the
+// overflow-free |g| > tol sqrt(a) sqrt(b).
+__device__ __forceinline__ bool rot_test_f32(float a, float b, float g, float tol, float tol2) {
+  const float lhs = g * g, rhs = tol2 * (a * b);
+  if (lhs < 1e30f && rhs < 1e30f && rhs > 1e-30f) return lhs > rhs;
+  return fabsf(g) > tol * (sqrtf(fmaxf(a, 0.f)) * sqrtf(fmaxf(b, 0.f)));
+}
+
+template <typename T>
+__device__ __forceinline__ bool rot_test(T a, T b, T g, double tol, double tol2) {
+  if constexpr (sizeof(T) == 4)
+    return rot_test_f32(a, b, g, (float)tol, (float)tol2);
+  else
+    return maybe_rotate(a, b, g, tol2) && exceeds(a, b, g, tol2);
+}
+
+// Rotation of one pair from its current Gram entries (a = g_ii, b = g_jj, g = g_ij),
+// stored in slot `sl` as pair k.  FP32 slices take the angle in FP32 (as the classical
+// single-precision one-sided Jacobi does: the rotation is applied to freshly formed
+// Grams, so the angle's rounding only affects the convergence rate); FP64 slices in FP64.
+//   zeta = (b - a) / (2 g);  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
+//     = sign(zeta) |2g| / (|b - a| + sqrt((b - a)^2 + 4 g^2))   (|t| <= 1)
+template <typename T, int W2, int NS, typename SM>
+__device__ __forceinline__ void pair_angle(SM &s, int sl, int k, int i, int j, T a, T b, T g,
+                                           double tol, double tol2) {
   s.pi[sl][k] = i;
   s.pj[sl][k] = j;
   s.pos[sl][i] = 2 * k;
@@ -282,17 +369,28 @@ __device__ __forceinline__ void pair_angle(Smem<T, W2, NS> &s, int sl, int k, in
   int rot = 0;
   if (!(isfinite(a) && isfinite(b))) {
     s.nonfinite = 1;
-  } else if (maybe_rotate((T)a, (T)b, (T)g, tol2) && g * g > tol2 * (a * b)) {
-    // zeta = (b - a) / (2 g);  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
-    //   = sign(zeta) |2g| / (|b - a| + sqrt((b - a)^2 + 4 g^2))   (one sqrt, one divide)
-    const double h = b - a, g2 = 2.0 * g;
-    const double sgn = ((h >= 0.0) == (g2 >= 0.0)) ? 1.0 : -1.0;
-    const double t = sgn * fabs(g2) / (fabs(h) + sqrt(h * h + g2 * g2));
-    const double c = rsqrt(1.0 + t * t);
-    s.cs[sl][2 * k] = (T)c;
-    s.cs[sl][2 * k + 1] = (T)(c * t);
-    s.dd[sl][2 * k] = (T)(a - t * g);
-    s.dd[sl][2 * k + 1] = (T)(b + t * g);
+  } else if (rot_test(a, b, g, tol, tol2)) {
+    if constexpr (sizeof(T) == 4) {
+      const float h = b - a, g2 = 2.f * g;
+      float t = fabsf(g2) / (fabsf(h) + hypotf(h, g2));
+      if ((h >= 0.f) != (g2 >= 0.f)) t = -t;
+      // correctly rounded 1/sqrt: an approximate reciprocal square root biased c (and the
+      // column norms, over thousands of rotations) by ~1e-5
+      const float c = __frsqrt_rn(fmaf(t, t, 1.f));
+      s.cs[sl][2 * k] = c;
+      s.cs[sl][2 * k + 1] = c * t;
+      s.dd[sl][2 * k] = fmaf(-t, g, a);
+      s.dd[sl][2 * k + 1] = fmaf(t, g, b);
+    } else {
+      const double h = b - a, g2 = 2.0 * g;
+      const double sgn = ((h >= 0.0) == (g2 >= 0.0)) ? 1.0 : -1.0;
+      const double t = sgn * fabs(g2) / (fabs(h) + sqrt(h * h + g2 * g2));
+      const double c = rsqrt(1.0 + t * t);
+      s.cs[sl][2 * k] = (T)c;
+      s.cs[sl][2 * k + 1] = (T)(c * t);
+      s.dd[sl][2 * k] = (T)(a - t * g);
+      s.dd[sl][2 * k + 1] = (T)(b + t * g);
+    }
     rot = 1;
     s.any_rot = 1;
     s.step_rot = 1;
@@ -312,29 +410,29 @@ __device__ __forceinline__ void pair_angle(Smem<T, W2, NS> &s, int sl, int k, in
 // written to the other) and to Q, the last warp already computes the angles of step s+1
 // from the Gram before step s and the rotations of step s, with the same 2 x 2
 // arithmetic the update warps use, so both see bit-identical entries.
-template <typename T, int W2, int NS>
-__device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool first) {
-  const int tid = threadIdx.x;
+template <typename T, int W2, int NS, typename SM, typename Bar>
+__device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, const Bar &bar) {
+  
   constexpr int NP = W2 / 2;
   constexpr int AW = NT / 32 - 1;          // the angle warp
   constexpr int NU = NT - 32;              // update threads
   const double tol2 = tol * tol;
   const int g0 = s.gcur;
-  // fresh-Gram convergence test: |g| > tol sqrt(a b)  <=>  g^2 > tol^2 a b  (FP64)
+  // fresh-Gram convergence test |g| > tol sqrt(a b) (the same test pair_angle applies)
   int need = 0;
   for (int idx = tid; idx < W2 * W2; idx += NT) {
     int i = idx / W2, j = idx % W2;
     if (i < j && (full || (i < NP && j >= NP))) {
       const T a = s.G[g0][tri<W2>(i, i)], b = s.G[g0][tri<W2>(j, j)], g = s.G[g0][tri<W2>(i, j)];
-      if (maybe_rotate(a, b, g, tol2) && exceeds(a, b, g, tol2)) need = 1;
+      if (rot_test(a, b, g, tol, tol2)) need = 1;
     }
   }
-  __syncthreads();                   // every thread has read step_rot of the previous call
+  bar.sync();                        // every thread has read step_rot of the previous call
   if (tid == 0) {
     s.step_rot = 0;
     if (first) s.any_rot = 0;
   }
-  if (!__syncthreads_or(need)) return;
+  if (!bar.sync_or(need)) return;
   if (first) {
     for (int idx = tid; idx < W2 * W2; idx += NT) s.Q[idx] = (idx / W2 == idx % W2) ? T(1) : T(0);
   }
@@ -343,10 +441,10 @@ __device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool firs
   if (warp == AW && lane < NP) {     // angles of step 0 from the fresh Gram
     int i, j;
     inner_pair<W2>(full, 0, lane, i, j);
-    pair_angle<T, W2, NS>(s, 0, lane, i, j, (double)s.G[g0][tri<W2>(i, i)],
-                          (double)s.G[g0][tri<W2>(j, j)], (double)s.G[g0][tri<W2>(i, j)], tol2);
+    pair_angle<T, W2, NS>(s, 0, lane, i, j, s.G[g0][tri<W2>(i, i)], s.G[g0][tri<W2>(j, j)],
+                          s.G[g0][tri<W2>(i, j)], tol, tol2);
   }
-  __syncthreads();
+  bar.sync();
   for (int step = 0; step < nsteps; ++step) {
     const int sl = step & 1;
     const T *Gs = s.G[g0 ^ (step & 1)];
@@ -374,7 +472,7 @@ __device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool firs
                     s.cs[sl][2 * ph + 1], o[0], o[1], o[2], o[3]);
           g = o[2 * rl + rh];
         }
-        pair_angle<T, W2, NS>(s, sl ^ 1, lane, i, j, (double)a, (double)b, (double)g, tol2);
+        pair_angle<T, W2, NS>(s, sl ^ 1, lane, i, j, a, b, g, tol, tol2);
       }
     } else {
       // G_{s+1} = J^T G_s J on the blocks pp <= qq (the rest is their transpose)
@@ -421,10 +519,10 @@ __device__ void inner_sweep(Smem<T, W2, NS> &s, double tol, bool full, bool firs
         s.Q[r * W2 + j] = sn * x + c * y;
       }
     }
-    __syncthreads();
+    bar.sync();
   }
   if (tid == 0) s.gcur = g0 ^ (nsteps & 1);
-  __syncthreads();
+  bar.sync();
 }
 
 // [Wsl(:, col)] <- [Wsl(:, col)] Q, rows streamed through the cp.async pipeline; results
@@ -496,6 +594,327 @@ __device__ void apply_q(Smem<T, W2, NS> &s, T *__restrict__ Wsl, int rows, int l
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- tensor-core products
+// The Gram enters the tensor cores as x = h + l, h = tf32(x), l = tf32(x - h) (x - h is
+// exact; |x - h - l| <= 2^-22 |x|): its rounding only steers the rotation angles and the
+// stopping test (whose threshold is ~4 sqrt(m) 2^-24), never the columns themselves.
+
+constexpr unsigned TC_SPIN = 1u << 22;
+
+// Bounded wait for the next completion of barrier b (phase bits in `phase`, identical in
+// every thread because every thread waits on every completion).  After one expiry the
+// CTA stops waiting; the host sees ST_TIMEOUT.
+__device__ __forceinline__ void tc_wait(SmemTc &s, int b, uint32_t &phase) {
+  const uint32_t par = (phase >> b) & 1u;
+  if (!*(volatile int *)&s.fail && !tc::mbar_wait(&s.bar[b], par, TC_SPIN)) s.fail = 1;
+  phase ^= 1u << b;
+}
+
+// Eight consecutive rows r .. r+7 of one column (zeros past `rows` or for padding).
+__device__ __forceinline__ void load8(const float *src, int r, int rows, bool vec, float (&v)[8]) {
+  if (src != nullptr && vec && r + 8 <= rows) {
+    const float4 a = __ldcg(reinterpret_cast<const float4 *>(src + r));
+    const float4 b = __ldcg(reinterpret_cast<const float4 *>(src + r + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = (src != nullptr && r + e < rows) ? __ldcg(src + r + e) : 0.f;
+  }
+}
+
+// 16-byte chunk `ch` (4 TF32 values) of row `row` of a K-major 128-byte-swizzled tile.
+__device__ __forceinline__ void put_chunk(unsigned char *tile, uint32_t row, uint32_t ch,
+                                          uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  *reinterpret_cast<uint4 *>(tile + row * 128 + ((ch ^ (row & 7)) << 4)) = make_uint4(a, b, c, d);
+}
+
+// G = W_c^T W_c of the 64 columns col[] on the tensor cores.  Rows stream in chunks of 32
+// (K); a chunk's tile holds H (rows 0..63, one per column) over L (rows 64..127), so one
+// MMA with A = the whole tile (M = 128) and B = its first 64 rows (N = 64) accumulates
+// [H^T H ; L^T H] in TMEM.  Then G = H^T H + L^T H + (L^T H)^T, summed in that order.
+// Two tiles alternate; the loads of chunk ck+1 are in flight while chunk ck is stored.
+__device__ void gram_tc(SmemTc &s, const float *__restrict__ Wsl, int rows, int lda,
+                        uint32_t &phase, int tid, const GroupBar &bar) {
+  constexpr int W2 = SmemTc::W2;
+  constexpr int GK = 32;
+  const int c = tid >> 2, q = tid & 3;             // column, 8-row quarter of the chunk
+  const bool vec = (lda & 3) == 0 && ((uintptr_t)Wsl & 15) == 0;
+  const int gc = s.col[c];
+  const float *src = gc >= 0 ? Wsl + (int64_t)gc * lda : nullptr;
+  const int nck = (rows + GK - 1) / GK;
+  const uint32_t idesc = tc::instr_desc(2, 128, W2);
+  float v[8], vn[8];
+  load8(src, q * 8, rows, vec, v);
+  for (int ck = 0; ck < nck; ++ck) {
+    const int b = ck & 1;
+    if (ck + 1 < nck) load8(src, (ck + 1) * GK + q * 8, rows, vec, vn);
+    if (ck >= 2) tc_wait(s, b, phase);             // the MMAs of chunk ck-2 read tile b
+    unsigned char *tile = s.op + b * 16384;
+    uint32_t h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      h[e] = tc::tf32_rna(v[e]);
+      l[e] = tc::tf32_rna(v[e] - __uint_as_float(h[e]));
+    }
+    put_chunk(tile, c, 2 * q, h[0], h[1], h[2], h[3]);
+    put_chunk(tile, c, 2 * q + 1, h[4], h[5], h[6], h[7]);
+    put_chunk(tile, 64 + c, 2 * q, l[0], l[1], l[2], l[3]);
+    put_chunk(tile, 64 + c, 2 * q + 1, l[4], l[5], l[6], l[7]);
+    tc::fence_proxy_async();
+    bar.sync();
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < GK / 8; ++kk) {
+        const uint64_t d = tc::smem_desc(tile + kk * 32, 1024, 2);
+        tc::mma_tf32(s.tmem, d, d, idesc, (ck > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&s.bar[b]);
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = vn[e];
+  }
+  for (int ck = nck >= 2 ? nck - 2 : 0; ck < nck; ++ck) tc_wait(s, ck & 1, phase);
+  tc::fence_after_sync();
+  // epilogue: warps 2, 3 park L^T H (TMEM lanes 64..127) in the tile area, XOR-swizzled
+  // S[i][j] at i*64 + (j ^ i) (conflict-free by rows and by columns); warps 0, 1 add it to
+  // their H^T H rows
+  float *S = reinterpret_cast<float *>(s.op);
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp == 2 || warp == 3) {
+    const int i = (warp - 2) * 32 + lane;
+#pragma unroll
+    for (int j0 = 0; j0 < W2; j0 += 16) {
+      float d[16];
+      tc::tmem_ld16(s.tmem + ((uint32_t)(warp * 32) << 16) + j0, d);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) S[i * 64 + ((j0 + e) ^ i)] = d[e];
+    }
+  }
+  tc::fence_before_sync();
+  bar.sync();
+  if (warp < 2) {
+    const int i = warp * 32 + lane;
+#pragma unroll
+    for (int j0 = 0; j0 < W2; j0 += 16) {
+      float d[16];
+      tc::tmem_ld16(s.tmem + ((uint32_t)(warp * 32) << 16) + j0, d);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int j = j0 + e;
+        if (j >= i) s.G[0][tri<W2>(i, j)] = (d[e] + S[i * 64 + (j ^ i)]) + S[j * 64 + (i ^ j)];
+      }
+    }
+  }
+  if (tid == 0) s.gcur = 0;
+  tc::fence_before_sync();
+  bar.sync();
+}
+
+// The rotation apply needs FP32 accuracy (its rounding accumulates in the columns over the
+// sweeps), so it splits every value into three BF16 terms x = x1 + x2 + x3 (each the
+// rounding of what the previous ones leave; |x - x1 - x2 - x3| <= 2^-27 |x|) and forms the
+// six products whose order is at least 2^-24: x1 y1, x1 y2, x2 y1, x1 y3, x3 y1, x2 y2.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &a, __nv_bfloat16 &b,
+                                       __nv_bfloat16 &c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+// 16-byte chunk `ch` (8 BF16 values) of row `row` of a K-major 64-byte-swizzled tile.
+__device__ __forceinline__ uint32_t sw64(uint32_t row, uint32_t ch) {
+  return row * 64 + ((ch ^ ((row >> 1) & 3)) << 4);
+}
+
+constexpr uint32_t AP_TERM = 8192;    // one term of the apply's A tile: [128 rows x 32 K] BF16
+constexpr uint32_t BQ_TERM = 8192;    // one term of (Q - I): 2 K-blocks x [64 x 32] BF16
+constexpr uint32_t BQ_KB = 4096;
+
+// B operand of the apply from the accumulated rotation: (Q - I)(c, c') split into three
+// BF16 terms, K-major (row c', K = c), two K-blocks of 32.  Overwrites G and Q.
+__device__ void build_bq(SmemTc &s, int tid, const GroupBar &bar) {
+  constexpr int W2 = SmemTc::W2;
+  float qv[W2 * W2 / NT];
+#pragma unroll
+  for (int m = 0; m < W2 * W2 / NT; ++m) {
+    const int idx = tid + NT * m, c = idx >> 6, cp = idx & 63;
+    qv[m] = s.Q[c * W2 + cp] - (c == cp ? 1.f : 0.f);
+  }
+  bar.sync();
+#pragma unroll
+  for (int m = 0; m < W2 * W2 / NT; ++m) {
+    const int idx = tid + NT * m, c = idx >> 6, cp = idx & 63;
+    __nv_bfloat16 t[3];
+    split3(qv[m], t[0], t[1], t[2]);
+    const uint32_t kb = (uint32_t)c >> 5, k = (uint32_t)c & 31;
+    const uint32_t off = kb * BQ_KB + sw64((uint32_t)cp, k >> 3) + (k & 7) * 2;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      *reinterpret_cast<__nv_bfloat16 *>(s.bq + u * BQ_TERM + off) = t[u];
+  }
+  tc::fence_proxy_async();
+  bar.sync();
+}
+
+// W(:, col) <- W(:, col) + W(:, col) (Q - I) on the tensor cores, 128 rows at a time.
+// Thread t owns row r = t mod 128 of the chunk and, in each K-block kb, the 16 columns
+// kb*32 + (t/128)*16 ..: it loads them, writes their three BF16 terms into the A tiles and,
+// after the MMAs, reads the same 16 columns of its TMEM lane and stores x + D.  Adding the
+// correction W (Q - I) in FP32 keeps the accumulator's rounding away from the columns'
+// norms (Q -> I as the sweeps converge).
+__device__ void apply_tc(SmemTc &s, float *__restrict__ W, int rows, int lda, uint32_t &phase,
+                         int tid, const GroupBar &bar) {
+  constexpr int W2 = SmemTc::W2;
+  // (A term, B term) of the six products
+  constexpr int PA[6] = {0, 0, 1, 0, 2, 1}, PB[6] = {0, 1, 0, 2, 0, 1};
+  const int warp = tid >> 5;
+  const int r = tid & 127, hh = tid >> 7;
+  const uint32_t idesc = tc::instr_desc(1, 128, W2);
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const int nck = (rows + 127) / 128;
+  for (int ck = 0; ck < nck; ++ck) {
+    const int row = ck * 128 + r;
+    const bool rin = row < rows;
+    float x[32];
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int gc = s.col[kb * 32 + hh * 16 + e];
+        x[kb * 16 + e] = (rin && gc >= 0) ? __ldcg(W + (int64_t)gc * lda + row) : 0.f;
+      }
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {
+      if (kb == 1) tc_wait(s, 2, phase);           // the K-block 0 MMAs read the tiles
+#pragma unroll
+      for (int h8 = 0; h8 < 2; ++h8) {              // 8 columns = one 16-byte chunk per term
+        uint32_t w[3][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+          split3(x[kb * 16 + h8 * 8 + e], a0, a1, a2);
+          split3(x[kb * 16 + h8 * 8 + e + 1], b0, b1, b2);
+          w[0][e / 2] = pack2(a0, b0);
+          w[1][e / 2] = pack2(a1, b1);
+          w[2][e / 2] = pack2(a2, b2);
+        }
+        const uint32_t off = sw64((uint32_t)r, (uint32_t)(hh * 2 + h8));
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          *reinterpret_cast<uint4 *>(s.op + u * AP_TERM + off) =
+              make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      bar.sync();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+          for (int m = 0; m < 6; ++m) {
+            const uint64_t a = tc::smem_desc(s.op + PA[m] * AP_TERM + kk * 32, 512, 4);
+            const uint64_t b =
+                tc::smem_desc(s.bq + PB[m] * BQ_TERM + kb * BQ_KB + kk * 32, 512, 4);
+            tc::mma_f16(s.tmem, a, b, idesc, (kb > 0 || kk > 0 || m > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&s.bar[2]);
+      }
+    }
+    tc_wait(s, 2, phase);                          // D complete, tiles free
+    tc::fence_after_sync();
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {
+      float d[16];
+      tc::tmem_ld16(s.tmem + lane_base + (uint32_t)(kb * 32 + hh * 16), d);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int gc = s.col[kb * 32 + hh * 16 + e];
+        if (rin && gc >= 0) __stcg(W + (int64_t)gc * lda + row, x[kb * 16 + e] + d[e]);
+      }
+    }
+    tc::fence_before_sync();
+    bar.sync();                                    // TMEM read before the next chunk's MMAs
+  }
+}
+
+// This slice's matrices: the uniform batch of one tensor, or a per-slice descriptor.
+template <typename T>
+struct SliceView {
+  T *W, *V;
+  float *nrm2;
+  int rows, cols;
+};
+template <typename T>
+__device__ __forceinline__ SliceView<T> slice_view(const JacobiParams &p, int slice) {
+  SliceView<T> v;
+  if (p.desc) {
+    const SliceDesc d = p.desc[slice];
+    v.W = reinterpret_cast<T *>(d.A);
+    v.V = reinterpret_cast<T *>(d.V);
+    v.nrm2 = d.norm2;
+    v.rows = d.rows;
+    v.cols = d.cols;
+  } else {
+    v.W = reinterpret_cast<T *>(p.A) + (int64_t)slice * p.sA;
+    v.V = reinterpret_cast<T *>(p.V) + (int64_t)slice * p.sV;
+    v.nrm2 = p.norm2 ? p.norm2 + (int64_t)slice * p.cols : nullptr;
+    v.rows = p.rows;
+    v.cols = p.cols;
+  }
+  return v;
+}
+
+// de Rijk ordering: s.ord = the columns by decreasing norm (ties: lower index first), from
+// the squared norms the previous sweep left in nrm (bitonic sort of a power-of-two key
+// array); the first sweep keeps 0..cols-1.
+template <typename SM, typename Bar>
+__device__ void sort_columns(SM &s, const float *nrm, int cols, bool first, int tid,
+                             const Bar &bar) {
+  int p2 = 1;
+  while (p2 < cols) p2 <<= 1;
+  float *key = sort_keys(s);
+  for (int c = tid; c < p2; c += NT) {
+    key[c] = c < cols ? (first ? -(float)c : __ldcg(nrm + c)) : -INFINITY;
+    s.ord[c] = c;
+  }
+  bar.sync();
+  for (int k = 2; k <= p2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = tid; t < p2; t += NT) {
+        int u = t ^ j;
+        if (u > t) {
+          float kt = key[t], ku = key[u];
+          int it = s.ord[t], iu = s.ord[u];
+          bool t_first = (kt > ku) || (kt == ku && it < iu);
+          if (((t & k) == 0) ? !t_first : t_first) {
+            key[t] = ku; key[u] = kt;
+            s.ord[t] = iu; s.ord[u] = it;
+          }
+        }
+      }
+      bar.sync();
+    }
+  }
+}
+
+// Local columns of block pair (bi, bj) of the sweep's order (-1 = padding).
+template <int W2, typename SM>
+__device__ __forceinline__ void pair_columns(SM &s, int bi, int bj, int cols, bool sorted,
+                                             int tid) {
+  constexpr int B = W2 / 2;
+  if (tid < W2) {
+    int lc = (tid < B) ? bi * B + tid : bj * B + (tid - B);
+    s.col[tid] = lc < cols ? (sorted ? s.ord[lc] : lc) : -1;
+  }
+}
+
 template <typename T, int W2, int NS>
 __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParams p) {
   using C = Cfg<T, W2, NS>;
@@ -506,6 +925,7 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
   const int csize = (int)cluster.num_blocks();
   const int tid = threadIdx.x;
   const double tol = p.tol;
+  const CtaBar bar;
 
   for (int iter = 0;; ++iter) {
     const int par = iter & 1;
@@ -513,92 +933,44 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
     cluster.sync();
     const int slice = *cluster.map_shared_rank(&s.slice[par], 0);
     if (slice >= p.nslices) break;
-    // this slice's matrices: uniform batch of one tensor, or a per-slice descriptor
-    T *Wsl, *Vsl;
-    float *nrm2;
-    int rows, cols;
-    if (p.desc) {
-      const SliceDesc d = p.desc[slice];
-      Wsl = reinterpret_cast<T *>(d.A);
-      Vsl = reinterpret_cast<T *>(d.V);
-      nrm2 = d.norm2;
-      rows = d.rows;
-      cols = d.cols;
-    } else {
-      Wsl = reinterpret_cast<T *>(p.A) + (int64_t)slice * p.sA;
-      Vsl = reinterpret_cast<T *>(p.V) + (int64_t)slice * p.sV;
-      nrm2 = p.norm2 ? p.norm2 + (int64_t)slice * p.cols : nullptr;
-      rows = p.rows;
-      cols = p.cols;
-    }
-    int nb = (cols + C::B - 1) / C::B;
+    const SliceView<T> v = slice_view<T>(p, slice);
+    int nb = (v.cols + C::B - 1) / C::B;
     if (nb & 1) ++nb;
     if (nb < 2) nb = 2;
 
     // V = I (this CTA initialises columns crank, crank + csize, ...)
-    for (int c = crank; c < cols; c += csize)
-      for (int r = tid; r < cols; r += NT) __stcg(Vsl + (int64_t)c * cols + r, r == c ? T(1) : T(0));
+    for (int c = crank; c < v.cols; c += csize)
+      for (int r = tid; r < v.cols; r += NT)
+        __stcg(v.V + (int64_t)c * v.cols + r, r == c ? T(1) : T(0));
     if (tid == 0) {
       s.nrot = 0;
       s.nonfinite = 0;
     }
     cluster.sync();
 
-    const bool sorted = nrm2 != nullptr && cols <= MAXSORT;
+    const bool sorted = v.nrm2 != nullptr && v.cols <= MAXSORT;
     int converged = 0, sweep = 0;
     for (sweep = 1; sweep <= p.max_sweeps; ++sweep) {
       if (tid == 0) s.sweep_any = 0;
-      if (sorted) {
-        // de Rijk ordering: columns by decreasing norm (ties: lower index first), from the
-        // squared norms the previous sweep left in norm2; the first sweep keeps 0..cols-1.
-        int p2 = 1;
-        while (p2 < cols) p2 <<= 1;
-        float *key = reinterpret_cast<float *>(s.buf);
-        const float *nrm = nrm2;
-        for (int c = tid; c < p2; c += NT) {
-          key[c] = c < cols ? (sweep == 1 ? -(float)c : __ldcg(nrm + c)) : -INFINITY;
-          s.ord[c] = c;
-        }
-        __syncthreads();
-        for (int k = 2; k <= p2; k <<= 1) {
-          for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = tid; t < p2; t += NT) {
-              int u = t ^ j;
-              if (u > t) {
-                float kt = key[t], ku = key[u];
-                int it = s.ord[t], iu = s.ord[u];
-                bool t_first = (kt > ku) || (kt == ku && it < iu);
-                if (((t & k) == 0) ? !t_first : t_first) {
-                  key[t] = ku; key[u] = kt;
-                  s.ord[t] = iu; s.ord[u] = it;
-                }
-              }
-            }
-            __syncthreads();
-          }
-        }
-      }
+      if (sorted) sort_columns(s, v.nrm2, v.cols, sweep == 1, tid, bar);
       for (int round = 0; round < nb - 1; ++round) {
         for (int q = crank; q < nb / 2; q += csize) {
           int bi, bj;
           rr_pair(nb, round, q, bi, bj);
-          if (tid < W2) {
-            int lc = (tid < C::B) ? bi * C::B + tid : bj * C::B + (tid - C::B);
-            s.col[tid] = lc < cols ? (sorted ? s.ord[lc] : lc) : -1;
-          }
+          pair_columns<W2>(s, bi, bj, v.cols, sorted, tid);
           __syncthreads();
-          gram<T, W2, NS>(s, Wsl, rows, rows);
+          gram<T, W2, NS>(s, v.W, v.rows, v.rows);
           for (int is = 0; is < p.inner_sweeps; ++is) {
-            inner_sweep<T, W2, NS>(s, tol, round == 0, is == 0);
+            inner_sweep<T, W2, NS>(s, tol, round == 0, is == 0, tid, bar);
             if (!s.step_rot) break;
           }
           __syncthreads();
           if (sorted && tid < W2 && s.col[tid] >= 0)     // squared norms after this step
-            __stcg(nrm2 + s.col[tid], (float)s.G[s.gcur][tri<W2>(tid, tid)]);
+            __stcg(v.nrm2 + s.col[tid], (float)s.G[s.gcur][tri<W2>(tid, tid)]);
           if (s.any_rot) {
             if (tid == 0) s.sweep_any = 1;
-            apply_q<T, W2, NS>(s, Wsl, rows, rows);
-            apply_q<T, W2, NS>(s, Vsl, cols, cols);
+            apply_q<T, W2, NS>(s, v.W, v.rows, v.rows);
+            apply_q<T, W2, NS>(s, v.V, v.cols, v.cols);
           }
           __syncthreads();
         }
@@ -625,6 +997,120 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
     }
   }
   cluster.sync();  // keep shared memory alive until every CTA has read the slice index
+}
+
+// ---------------------------------------------------------------- tensor-core kernel
+// A kernel that holds tensor memory runs one CTA per SM, so the tensor-core variant is one
+// persistent CTA per SM made of TC_GROUPS 256-thread groups.  Each group is a block-pair
+// worker with its own shared memory (SmemTc), named barrier, MMA barriers and 64 TMEM
+// columns; the groups of an SM overlap one another's latency-bound Gram sweeps with their
+// tensor-core products.  gps = groups per slice: 1 (every group factors whole slices of
+// its own; nothing is shared between groups) or TC_GROUPS (the CTA's groups share one
+// slice and split each round's block pairs; a CTA barrier per round).
+constexpr int TC_GROUPS = 3;
+constexpr uint32_t TC_COLS = 256;     // TMEM columns of the CTA (64 per group, power of two)
+
+__global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiParams p, int gps) {
+  constexpr int W2 = SmemTc::W2;
+  constexpr int B = W2 / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t tmem_base;
+  // the swizzled operand tiles need 1024-byte alignment (the launch adds the slack)
+  SmemTc *groups =
+      reinterpret_cast<SmemTc *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
+  SmemTc &s = groups[g];
+  const GroupBar gbar{1 + g};
+  const double tol = p.tol;
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) tc::mbar_init(&s.bar[b], 1);
+    tc::mbar_init_fence();
+    s.fail = 0;
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc_n<TC_COLS>(&tmem_base);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid == 0) s.tmem = tmem_base + 64u * (uint32_t)g;
+  gbar.sync();
+
+  const bool shared_slice = gps > 1;
+  const int lead = shared_slice ? g : 0;          // index of this group among its slice's
+  const int nlead = shared_slice ? TC_GROUPS : 1;
+  SmemTc &s0 = shared_slice ? groups[0] : s;      // holds the slice index
+  uint32_t phase = 0;
+  for (int iter = 0;; ++iter) {
+    const int par = iter & 1;
+    if (lead == 0 && tid == 0) s0.slice[par] = atomicAdd(p.queue, 1);
+    if (shared_slice) __syncthreads(); else gbar.sync();
+    const int slice = s0.slice[par];
+    if (slice >= p.nslices) break;
+    const SliceView<float> v = slice_view<float>(p, slice);
+    int nb = (v.cols + B - 1) / B;
+    if (nb & 1) ++nb;
+    if (nb < 2) nb = 2;
+    for (int c = lead; c < v.cols; c += nlead)      // V = I
+      for (int r = tid; r < v.cols; r += NT)
+        __stcg(v.V + (int64_t)c * v.cols + r, r == c ? 1.f : 0.f);
+    if (tid == 0) {
+      s.nrot = 0;
+      s.nonfinite = 0;
+    }
+    if (shared_slice) __syncthreads(); else gbar.sync();
+
+    const bool sorted = v.nrm2 != nullptr && v.cols <= MAXSORT;
+    int converged = 0, sweep = 0;
+    for (sweep = 1; sweep <= p.max_sweeps; ++sweep) {
+      if (tid == 0) s.sweep_any = 0;
+      if (sorted) sort_columns(s, v.nrm2, v.cols, sweep == 1, tid, gbar);
+      for (int round = 0; round < nb - 1; ++round) {
+        for (int q = lead; q < nb / 2; q += nlead) {
+          int bi, bj;
+          rr_pair(nb, round, q, bi, bj);
+          pair_columns<W2>(s, bi, bj, v.cols, sorted, tid);
+          gbar.sync();
+          gram_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
+          for (int is = 0; is < p.inner_sweeps; ++is) {
+            inner_sweep<float, W2, 2>(s, tol, round == 0, is == 0, tid, gbar);
+            if (!s.step_rot) break;
+          }
+          gbar.sync();
+          if (sorted && tid < W2 && s.col[tid] >= 0)     // squared norms after this step
+            __stcg(v.nrm2 + s.col[tid], s.G[s.gcur][tri<W2>(tid, tid)]);
+          if (s.any_rot) {
+            if (tid == 0) s.sweep_any = 1;
+            build_bq(s, tid, gbar);
+            apply_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
+            apply_tc(s, v.V, v.cols, v.cols, phase, tid, gbar);
+          }
+          gbar.sync();
+        }
+        if (shared_slice) {
+          __threadfence();
+          __syncthreads();
+        }
+      }
+      // did any group of this slice rotate during the sweep?
+      const int any = shared_slice ? __syncthreads_or(s.sweep_any) : gbar.sync_or(s.sweep_any);
+      if (!any) {
+        converged = 1;
+        break;
+      }
+    }
+    if (tid == 0) {
+      atomicAdd((unsigned long long *)&p.rots[slice], (unsigned long long)s.nrot);
+      if (s.nonfinite) atomicOr(p.status, ST_NONFINITE);
+      if (lead == 0) {
+        p.sweeps[slice] = converged ? sweep : -1;
+        if (!converged) atomicOr(p.status, ST_NOCONV);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();                                 // every group has finished
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc_n<TC_COLS>(tmem_base);
+  if (tid == 0 && s.fail) atomicOr(p.status, ST_TIMEOUT);
 }
 
 template <typename T, int W2, int NS>
@@ -668,6 +1154,34 @@ cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hi
   if (nclusters < 1) nclusters = 1;
   cfg.gridDim = dim3(nclusters * cl);
   return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+// gps_hint: groups per slice (1 or TC_GROUPS; 0 = one group per slice when there are at
+// least two slices per SM, else the CTA's groups share a slice); grid_hint: CTAs.
+cudaError_t launch_jacobi_tc(const JacobiParams &p, cudaStream_t st, int gps_hint,
+                             int grid_hint) {
+  static_assert(TC_GROUPS * sizeof(SmemTc) + 1024 <= 227 * 1024, "shared memory of a CTA");
+  const size_t smem = (size_t)TC_GROUPS * sizeof(SmemTc) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(jacobi_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_tc_kernel, NT * TC_GROUPS,
+                                                     smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int gps = gps_hint == 1 || gps_hint == TC_GROUPS
+                ? gps_hint
+                : (p.nslices >= 2 * sms ? 1 : TC_GROUPS);
+  // every SM (one group per slice: fewer busy groups per SM run faster than packed ones)
+  int grid = grid_hint > 0 ? grid_hint : sms * per_sm;
+  if (grid > p.nslices) grid = p.nslices;
+  if (grid < 1) grid = 1;
+  jacobi_tc_kernel<<<grid, NT * TC_GROUPS, smem, st>>>(p, gps);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- finalize
@@ -836,6 +1350,13 @@ __global__ void transpose_kernel(const T *__restrict__ A, int64_t m, int64_t p, 
 template <typename T>
 cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, int cluster_hint,
                        int grid_hint, int stages) {
+  if constexpr (sizeof(T) == 4) {
+    // tensor-core Gram / apply: block pairs of 64 columns (slices of >= 64 columns under
+    // the automatic choice; any width when asked for explicitly)
+    if (p.engine == JACOBI_TC || (p.engine == JACOBI_AUTO && p.cols >= 64 &&
+                                  (width_hint == 0 || width_hint == 64)))
+      return launch_jacobi_tc(p, st, cluster_hint, grid_hint);
+  }
   int w = width_hint;
   if (w != 16 && w != 32 && w != 64) w = p.cols <= 8 ? 16 : (p.cols <= 16 || p.cols < 256 ? 32 : 64);
   const bool two = stages == 2 || (stages == 0 && w == 64);

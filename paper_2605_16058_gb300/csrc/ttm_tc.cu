@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace tsvdm {
 namespace {
@@ -49,35 +50,21 @@ struct TcParams {
   uint32_t tmem_cols;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+using tc::mbar_arrive;
+using tc::mbar_expect_tx;
+using tc::mbar_init;
+using tc::mma_commit;
+using tc::mma_f16;
+using tc::mma_tf32;
+using tc::smem_desc;
+using tc::smem_u32;
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-// Bounded wait for the phase with parity `par`; returns false on expiry.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t par) {
-  uint32_t a = smem_u32(bar);
-  for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(par)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
+  return tc::mbar_wait(bar, par, SPIN_LIMIT);
+}
+// M = 128 (one CTA's row tile), N = n
+__device__ __forceinline__ uint32_t instr_desc(uint32_t fmt, uint32_t n) {
+  return tc::instr_desc(fmt, TBM, n);
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -86,44 +73,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
       "{%3, %4}], [%2];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// UMMA shared-memory descriptor: K-major, swizzled; sbo = byte stride between 8-row groups.
-__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t sbo, uint32_t layout) {
-  uint64_t d = 0;
-  d |= (uint64_t)((smem_u32(p) >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                          // leading byte offset (unused, K-major)
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;                          // descriptor version
-  d |= (uint64_t)layout << 61;                     // 2 = 128B swizzle, 4 = 64B swizzle
-  return d;
-}
-
-// Instruction descriptor: D FP32, A/B format `fmt` (1 = BF16 for kind::f16, 2 = TF32 for
-// kind::tf32), both K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t instr_desc(uint32_t fmt, uint32_t n) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                        uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
       : "memory");
 }
 

@@ -18,6 +18,8 @@ OK, EINVAL, ENOTORTHO, ENOCONV, ENONFINITE, ETIMEOUT, ENOMEM, ECAPACITY, ECUDA, 
 F32, F64 = 0, 1
 P_FP64, P_FP32, P_TF32, P_BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": P_FP64, "fp32": P_FP32, "tf32": P_TF32, "bf16x3": P_BF16X3}
+JACOBI_AUTO, JACOBI_FMA, JACOBI_TC = 0, 1, 2
+ENGINES = {"auto": JACOBI_AUTO, "fma": JACOBI_FMA, "tc": JACOBI_TC}
 
 # every symbol include/tsvdm.h declares, with (restype, argtypes)
 _i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -27,6 +29,7 @@ SIGNATURES = {
     "tsvdm_plan_destroy": (_i32, [_vp]),
     "tsvdm_plan_set_jacobi": (_i32, [_vp, _dbl, _i32]),
     "tsvdm_plan_set_tuning": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
+    "tsvdm_plan_set_engine": (_i32, [_vp, _i32]),
     "tsvdm_transform": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "tsvdm_fixed_rank": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pdbl]),
     "tsvdm_tolerance": (_i32, [_vp, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _vp, _i64, _pi64, _pdbl]),
@@ -121,6 +124,11 @@ def tsvdm_plan_set_tuning(plan, block_width=0, cluster_size=0, clusters=0, stage
                                              int(clusters), int(stages), int(ordering),
                                              int(inner_sweeps)),
                  "tsvdm_plan_set_tuning")
+
+
+def tsvdm_plan_set_engine(plan, engine):
+    e = ENGINES[engine] if isinstance(engine, str) else int(engine)
+    return check(lib().tsvdm_plan_set_engine(plan, e), "tsvdm_plan_set_engine")
 
 
 def tsvdm_transform(plan, X, M, inverse, Y):

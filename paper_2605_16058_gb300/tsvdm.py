@@ -59,6 +59,10 @@ class Plan:
     def set_jacobi(self, tol=0.0, max_sweeps=0):
         N.tsvdm_plan_set_jacobi(self.handle, tol, max_sweeps)
 
+    def set_engine(self, engine):
+        """Engine of the Jacobi Gram / rotation products: "auto", "fma" or "tc"."""
+        N.tsvdm_plan_set_engine(self.handle, engine)
+
     def transform(self, X, M, inverse=False, out=None):
         out = out if out is not None else torch.empty_like(X)
         N.tsvdm_transform(self.handle, X, M, int(inverse), out)

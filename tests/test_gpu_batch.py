@@ -116,8 +116,8 @@ def test_batch_run_graph_replay_and_autotuner(prec):
         for t, (S0, U0, r0) in zip(keep, first):
             assert torch.equal(t["S"], S0) and torch.equal(t["U"], U0) and torch.equal(t["rel"], r0)
         choice = N.tsvdm_batch_tune(b, ios)
-        assert choice["width"] in (32, 64) and choice["cluster"] in (1, 2, 4)
-        assert choice["stages"] in (2, 3) and choice["jacobi_ms"] > 0
+        assert choice["width"] in (32, 64) and choice["cluster"] in (1, 2, 3, 4)
+        assert choice["stages"] in (0, 2, 3) and choice["jacobi_ms"] > 0   # 0: tensor cores
         N.tsvdm_batch_run(b, ios)
         torch.cuda.synchronize()
         _check(keep)

@@ -104,8 +104,7 @@ def _compare_factors(dt, S_o, U_o, V_o, S_g, U_g, V_g, k):
                 assert proj_diff(V_o[:, :kk, i], V_g[:, :kk, i]) <= tol["proj"], (i, kk)
 
 
-@pytest.mark.parametrize("name,shape,dt,k", CASES_I, ids=[c[0] for c in CASES_I])
-def test_fixed_rank_matches_oracle(name, shape, dt, k):
+def _fixed_rank_case(name, shape, dt, k, engine=None):
     X, M = _case_input(name, shape)
     n1, n2, n3 = X.shape
     if dt == torch.float32:
@@ -113,6 +112,8 @@ def test_fixed_rank_matches_oracle(name, shape, dt, k):
         M = M.astype(np.float32).astype(np.float64)
     ref = oracle.fixed_rank(X, M, k)
     plan = _plan(n1, n2, n3, dt)
+    if engine is not None:
+        plan.set_engine(engine)
     out = plan.fixed_rank(t_lib(X, dtype=dt), t_lib(M, dtype=dt), k)
     U_g, S_g, V_g = np_lib(out["U"]), np_lib(out["S"]), np_lib(out["V"])
     assert U_g.shape == (n1, k, n3) and S_g.shape == (k, n3) and V_g.shape == (n2, k, n3)
@@ -124,6 +125,36 @@ def test_fixed_rank_matches_oracle(name, shape, dt, k):
         nz = S_g[:, i] > 1e-6 * max(S_g[0, i], 1e-300)
         u = U_g[:, nz, i]
         assert np.linalg.norm(u.T @ u - np.eye(u.shape[1])) < (1e-4 if dt == torch.float32 else 1e-10)
+
+
+@pytest.mark.parametrize("name,shape,dt,k", CASES_I, ids=[c[0] for c in CASES_I])
+def test_fixed_rank_matches_oracle(name, shape, dt, k):
+    _fixed_rank_case(name, shape, dt, k)
+
+
+# Both engines of the Jacobi products on every FP32 case: "tc" forced also on slices
+# narrower than a 64-column block pair (padding columns) and on row counts that are not a
+# multiple of 4 (the unvectorised load path), "fma" on slices the automatic choice sends
+# to the tensor cores.
+CASES_ENGINE = [c for c in CASES_I if c[2] == torch.float32]
+
+
+@pytest.mark.parametrize("engine", ["tc", "fma"])
+@pytest.mark.parametrize("name,shape,dt,k", CASES_ENGINE, ids=[c[0] for c in CASES_ENGINE])
+def test_fixed_rank_each_engine(name, shape, dt, k, engine):
+    _fixed_rank_case(name, shape, dt, k, engine)
+
+
+def test_engine_argument_errors():
+    from paper_2605_16058_gb300 import native as N
+    p64 = _plan(8, 8, 2, torch.float64)
+    with pytest.raises(N.TsvdmError) as e:
+        p64.set_engine("tc")
+    assert e.value.status == N.ENOTSUP
+    p32 = _plan(8, 8, 2, torch.float32)
+    with pytest.raises(N.TsvdmError) as e:
+        N.tsvdm_plan_set_engine(p32.handle, 7)
+    assert e.value.status == N.EINVAL
 
 
 @pytest.mark.parametrize("dt", [torch.float32, torch.float64])
