@@ -83,12 +83,9 @@ __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 // Packed upper triangle of a symmetric W2 x W2 matrix: entry (i, j), i <= j.
 template <int W2>
 __device__ __forceinline__ int tri(int i, int j) {
-  if (i > j) {
-    int t = i;
-    i = j;
-    j = t;
-  }
-  return (i * (2 * W2 - i + 1)) / 2 + (j - i);
+  const int lo = min(i, j), hi = max(i, j);
+  // row lo starts at lo W2 - lo (lo - 1) / 2; lo (2 W2 - 1 - lo) is even
+  return hi + (int)(((unsigned)lo * (unsigned)(2 * W2 - 1 - lo)) >> 1);
 }
 
 // The 2 x 2 block of G on rows (pair p) x columns (pair q) after J_p^T B J_q, written
@@ -438,6 +435,26 @@ __device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, c
   }
   const int nsteps = full ? W2 - 1 : NP;
   const int warp = tid >> 5, lane = tid & 31;
+  // the 2 x 2 blocks (pp <= qq) of pair slots this update thread owns in every step:
+  // block blk = tid + t NU, rows of the packed upper triangle of an NP x NP grid
+  constexpr int NB = NP * (NP + 1) / 2;
+  constexpr int BPT = (NB + NU - 1) / NU;
+  int bpp[BPT], bqq[BPT];
+#pragma unroll
+  for (int t = 0; t < BPT; ++t) {
+    const int blk = tid + t * NU;
+    bpp[t] = -1;
+    bqq[t] = 0;
+    if (warp != AW && blk < NB) {
+      int pp = 0, start = 0;
+      while (start + (NP - pp) <= blk) {
+        start += NP - pp;
+        ++pp;
+      }
+      bpp[t] = pp;
+      bqq[t] = pp + (blk - start);
+    }
+  }
   if (warp == AW && lane < NP) {     // angles of step 0 from the fresh Gram
     int i, j;
     inner_pair<W2>(full, 0, lane, i, j);
@@ -476,15 +493,10 @@ __device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, c
       }
     } else {
       // G_{s+1} = J^T G_s J on the blocks pp <= qq (the rest is their transpose)
-      constexpr int NB = NP * (NP + 1) / 2;
-      for (int blk = tid; blk < NB; blk += NU) {
-        // blk -> (pp, qq), pp <= qq: rows of the packed upper triangle of an NP x NP grid
-        int pp = (int)((2.0f * NP + 1.0f - sqrtf((2.0f * NP + 1.0f) * (2.0f * NP + 1.0f) -
-                                                  8.0f * blk)) * 0.5f);
-        if (pp < 0) pp = 0;
-        while (pp > 0 && pp * (2 * NP - pp + 1) / 2 > blk) --pp;
-        while ((pp + 1) * (2 * NP - pp) / 2 <= blk) ++pp;
-        const int qq = pp + (blk - pp * (2 * NP - pp + 1) / 2);
+#pragma unroll
+      for (int t = 0; t < BPT; ++t) {
+        const int pp = bpp[t], qq = bqq[t];
+        if (pp < 0) continue;
         const int i1 = s.pi[sl][pp], j1 = s.pj[sl][pp];
         if (pp == qq) {
           if (s.rot[sl][pp]) {
@@ -508,15 +520,18 @@ __device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, c
         Gd[tri<W2>(j1, i2)] = o10;
         Gd[tri<W2>(j1, j2)] = o11;
       }
-      // Q <- Q J  (lanes walk the pairs of one row: distinct columns of that row)
-      for (int it = tid; it < W2 * NP; it += NU) {
-        int r = it / NP, qq = it % NP;
-        if (!s.rot[sl][qq]) continue;
-        int i = s.pi[sl][qq], j = s.pj[sl][qq];
-        T c = s.cs[sl][2 * qq], sn = s.cs[sl][2 * qq + 1];
-        T x = s.Q[r * W2 + i], y = s.Q[r * W2 + j];
-        s.Q[r * W2 + i] = c * x - sn * y;
-        s.Q[r * W2 + j] = sn * x + c * y;
+      // Q <- Q J: lane -> pair k = lane mod NP and a row offset; a warp covers 32 / NP rows
+      // at a time (distinct columns of a row across the pairs)
+      constexpr int RPW = 32 / NP;
+      const int k = lane % NP;
+      if (s.rot[sl][k]) {
+        const int i = s.pi[sl][k], j = s.pj[sl][k];
+        const T c = s.cs[sl][2 * k], sn = s.cs[sl][2 * k + 1];
+        for (int r = warp * RPW + lane / NP; r < W2; r += (NU / 32) * RPW) {
+          const T x = s.Q[r * W2 + i], y = s.Q[r * W2 + j];
+          s.Q[r * W2 + i] = c * x - sn * y;
+          s.Q[r * W2 + j] = sn * x + c * y;
+        }
       }
     }
     bar.sync();
