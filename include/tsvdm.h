@@ -120,10 +120,10 @@ tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster
  *                      Apply: W + W (Q - I) with W and Q - I split into three BF16 terms
  *                      (x1 + x2 + x3, residual <= 2^-27 |x|) and the six products of order
  *                      >= 2^-24.  FP32 accumulation.  Block pairs are 64 columns.
- *                      One persistent CTA per SM of three 256-thread workers; under
- *                      tsvdm_plan_set_tuning, cluster_size is the number of workers that
- *                      share a slice (1 or 3; 0 = 1 when there are at least two slices per
- *                      SM, else 3), clusters the CTAs launched, stages is ignored.
+ *                      One persistent CTA per SM of three 256-thread workers that take
+ *                      block pairs of any slice in progress (dataflow order within a
+ *                      slice); under tsvdm_plan_set_tuning, clusters caps the CTAs
+ *                      launched, cluster_size and stages are ignored.
  * AUTO uses TC for F32 slices of at least 64 columns unless block_width asks for 16 or 32.
  * ENOTSUP for TC on an F64 plan, EINVAL for other values. */
 typedef enum {
@@ -291,12 +291,11 @@ tsvdm_status tsvdm_batch_capture(tsvdm_batch b, const tsvdm_batch_io *io);
 /* Replays the captured graph on the batch's stream. */
 tsvdm_status tsvdm_batch_launch(tsvdm_batch b);
 /* Autotuner: times the Jacobi launch for each candidate (F32 batches whose slices all
- * have >= 64 columns: the tensor-core engine with 1 or 3 worker groups per slice; and the
- * FMA engine with block width 32/64, cluster size 1/2/4, pipeline stages 2/3) on these
- * inputs and keeps the fastest; choice (nullable, int[4]) receives width, cluster size
- * (groups per slice for the tensor-core engine), stages (0 = the tensor-core engine) and
- * the best time in microseconds.  Until tuned, a batch uses TSVDM_JACOBI_AUTO
- * (tsvdm_plan_set_engine). */
+ * have >= 64 columns: the tensor-core engine; and the FMA engine with block width 32/64,
+ * cluster size 1/2/4, pipeline stages 2/3) on these inputs and keeps the fastest; choice
+ * (nullable, int[4]) receives width, cluster size, stages (0 = the tensor-core engine,
+ * reported with cluster size 1) and the best time in microseconds.  Until tuned, a batch
+ * uses TSVDM_JACOBI_AUTO (tsvdm_plan_set_engine). */
 tsvdm_status tsvdm_batch_tune(tsvdm_batch b, const tsvdm_batch_io *io, int *choice);
 /* Synchronises; sweeps and rotations summed over all slices of the last run, and the
  * device-detected status (ENOCONV, ENONFINITE, ETIMEOUT or OK, then cleared). */

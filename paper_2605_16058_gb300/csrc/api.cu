@@ -28,6 +28,8 @@ struct tsvdm_plan_s {
   int64_t *off_ws = nullptr;
   long long *rots = nullptr;
   float *norm2 = nullptr;
+  void *sched = nullptr;
+  size_t sched_bytes = 0;
   int sort_cols = 1;
   double *scal = nullptr;
   double *splitk = nullptr;
@@ -197,6 +199,9 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   jp.inner_sweeps = p->inner_sweeps;
   jp.desc = nullptr;
   jp.engine = p->engine;
+  jp.sched = p->sched;
+  jp.sched_bytes = p->sched_bytes;
+  jp.max_cols = (int)p->cols;
   stage_begin(p, TSVDM_STAGE_JACOBI);
   CK(jacobi_run<T>(jp, p->st, p->width_hint, p->cluster_hint, p->grid_hint, p->stages_hint));
   stage_end(p, TSVDM_STAGE_JACOBI, 1);
@@ -373,7 +378,7 @@ bool valid_plan(tsvdm_plan p) { return p != nullptr && p->Ahat != nullptr; }
 void free_plan(tsvdm_plan_s *p) {
   void *bufs[] = {p->Ahat, p->Wt, p->Vw, p->sig, p->keys, p->perm, p->sweeps, p->status,
                   p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk, p->tc_ws,
-                  p->norm2};
+                  p->norm2, p->sched};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < STG_COUNT; ++i)
@@ -454,6 +459,8 @@ tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype d
   AL(p->norm2, sizeof(float) * ns);
   AL(p->status, sizeof(int));
   AL(p->queue, sizeof(int));
+  p->sched_bytes = jacobi_sched_bytes(n3, p->cols);
+  AL(p->sched, p->sched_bytes);
   AL(p->ranks_ws, sizeof(int) * n3);
   AL(p->off_ws, sizeof(int64_t) * (n3 + 1));
   AL(p->scal, sizeof(double) * SC_COUNT);

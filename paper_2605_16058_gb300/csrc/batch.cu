@@ -82,6 +82,8 @@ struct tsvdm_batch_s {
   void *tc_ws = nullptr;
   size_t tc_ws_bytes = 0;
   int *status = nullptr, *queue = nullptr, *sweeps = nullptr;
+  void *sched = nullptr;
+  size_t sched_bytes = 0;
   long long *rots = nullptr;
   std::vector<RelErrArg> h_rel;
   // Jacobi launch shape (autotuned)
@@ -139,6 +141,9 @@ tsvdm_status run_batch(tsvdm_batch_s *b, const tsvdm_batch_io *io, bool timed) {
   jp.inner_sweeps = 2;
   jp.desc = b->desc;
   jp.engine = b->engine;
+  jp.sched = b->sched;
+  jp.sched_bytes = b->sched_bytes;
+  jp.max_cols = b->max_cols;
   if (timed) CKB(cudaEventRecord(b->ev[0], st));
   CKB(jacobi_run<T>(jp, st, b->width, b->cluster, b->clusters, b->stages));
   if (timed) CKB(cudaEventRecord(b->ev[1], st));
@@ -197,7 +202,8 @@ void free_batch(tsvdm_batch_s *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   void *bufs[] = {b->arena, b->iarena, b->farena, b->larena, b->karena, b->darena, b->desc,
-                  b->segs, b->relargs, b->tc_ws, b->status, b->queue, b->sweeps, b->rots};
+                  b->segs, b->relargs, b->tc_ws, b->status, b->queue, b->sweeps, b->rots,
+                  b->sched};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &e : b->ev)
@@ -280,6 +286,8 @@ tsvdm_status tsvdm_batch_create(const tsvdm_batch_desc *descs, int count, tsvdm_
   ALB(b->queue, sizeof(int));
   ALB(b->sweeps, sizeof(int) * b->total_slices);
   ALB(b->rots, sizeof(long long) * b->total_slices);
+  b->sched_bytes = jacobi_sched_bytes(b->total_slices, b->max_cols);
+  ALB(b->sched, b->sched_bytes);
   if (prec == TSVDM_P_TF32 || prec == TSVDM_P_BF16X3) {
     b->tc_ws_bytes = ttm_tc_workspace(max_n3, max_n3);
     ALB(b->tc_ws, b->tc_ws_bytes);
@@ -439,7 +447,7 @@ tsvdm_status tsvdm_batch_tune(tsvdm_batch b, const tsvdm_batch_io *io, int *choi
   const int clusters[3] = {1, 2, 4};
   const int stages[2] = {2, 3};
   if (b->dtype == TSVDM_F32 && b->min_cols >= 64)     // tensor-core Gram / apply
-    for (int gps : {1, 3}) cands.push_back({64, gps, 0, JACOBI_TC});
+    cands.push_back({64, 1, 0, JACOBI_TC});
   for (int w : widths) {
     if (w == 64 && b->min_cols < 64) continue;
     for (int c : clusters)

@@ -80,12 +80,17 @@ struct JacobiParams {
   int inner_sweeps;    // Gram sweeps per block pair (>= 1)
   const SliceDesc *desc; // per-slice matrices (batched), or nullptr (uniform, A/V/sA/sV)
   int engine;          // JACOBI_AUTO / JACOBI_FMA / JACOBI_TC (Gram and apply products)
+  void *sched;         // tensor-core kernel's scheduler state (jacobi_sched_bytes), zeroed
+  size_t sched_bytes;  //   by jacobi_run before the launch
+  int max_cols;        // largest cols of any slice (sizes the scheduler state)
 };
 enum { JACOBI_AUTO = 0, JACOBI_FMA = 1, JACOBI_TC = 2 };
 
 template <typename T>
 cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, int cluster_hint,
                        int grid_hint, int stages);
+// Scheduler state of the tensor-core Jacobi for nslices slices of at most max_cols columns.
+size_t jacobi_sched_bytes(int64_t nslices, int64_t max_cols);
 
 // sigma (sorted descending) and the column permutation of each slice.
 template <typename T>

@@ -182,6 +182,8 @@ struct SmemTc {
   uint64_t bar[3];                         // MMA completion: Gram tiles 0 and 1, apply
   uint32_t tmem;                           // TMEM base (64 FP32 columns x 128 lanes)
   int fail;                                // a bounded wait ran out
+  int wk[4];                               // work item broadcast to the group
+  int reopen;                              // this worker closed a sweep that continues
 };
 
 template <typename SM>
@@ -1016,18 +1018,80 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
 
 // ---------------------------------------------------------------- tensor-core kernel
 // A kernel that holds tensor memory runs one CTA per SM, so the tensor-core variant is one
-// persistent CTA per SM made of TC_GROUPS 256-thread groups.  Each group is a block-pair
-// worker with its own shared memory (SmemTc), named barrier, MMA barriers and 64 TMEM
-// columns; the groups of an SM overlap one another's latency-bound Gram sweeps with their
-// tensor-core products.  gps = groups per slice: 1 (every group factors whole slices of
-// its own; nothing is shared between groups) or TC_GROUPS (the CTA's groups share one
-// slice and split each round's block pairs; a CTA barrier per round).
+// persistent CTA per SM made of TC_GROUPS 256-thread groups ("workers").  Each worker has
+// its own shared memory (SmemTc), named barrier, MMA barriers and 64 TMEM columns.
+//
+// Work is scheduled GPU-wide at the granularity of one block pair, so that slices whose
+// iteration runs longer than others do not leave SMs idle at the end.  Per slice (SliceCtx
+// in global memory): sn = (sweep << 32) | next ticket, a ticket t of sweep w being the
+// block pair q = t mod np of round t / np (np = nb / 2 pairs, nb - 1 rounds); done = pairs
+// of the sweep completed; rot = whether a pair rotated.  Per block: a version counter = the
+// pairs that have finished with it.  Block b enters exactly one pair per round, so the pair
+// of round r of sweep w may start when both its blocks have version (w - 1)(nb - 1) + r;
+// tickets are handed out in increasing order and a pair only waits for pairs with smaller
+// tickets, so the earliest unfinished ticket can always run (no deadlock).  The worker that
+// completes the last pair of a sweep closes it: the slice has converged if no pair rotated
+// (the stopping rule of the scalar method), else it copies the squared column norms the
+// sweep left into a per-slice snapshot and opens the next sweep's tickets (every worker
+// sorts the sweep's column order from the snapshot, so all agree on the blocks while the
+// sweep's own pairs keep updating the norms).  A worker takes a
+// ticket from its current slice, else starts a new slice, else helps any open slice; a
+// ticket more than one round ahead of the completed ones is left to others.  Every wait is
+// bounded; on expiry the kernel raises a global abort flag and ST_TIMEOUT.
 constexpr int TC_GROUPS = 3;
 constexpr uint32_t TC_COLS = 256;     // TMEM columns of the CTA (64 per group, power of two)
+constexpr unsigned SCHED_SPIN = 1u << 24;   // polls of a dependency or idle wait (~1 us each)
 
-__global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiParams p, int gps) {
+struct SliceCtx {
+  unsigned long long sn;   // (sweep << 32) | next ticket; sweep 0 = not started
+  int done;                // pairs of the current sweep completed
+  int rot[2];              // a pair rotated, by sweep parity
+  int finished;            // converged or capped
+  int pad[2];
+};
+struct SchedHdr {
+  int fin;                 // slices finished
+  int abort;               // a wait ran out: everybody leaves
+  int pad[14];
+};
+
+__host__ __device__ inline int tc_blocks(int cols) {
+  int nb = (cols + 31) / 32;
+  if (nb & 1) ++nb;
+  return nb < 2 ? 2 : nb;
+}
+
+enum { WK_EXIT = 0, WK_START = 1, WK_PAIR = 2 };
+
+__device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ unsigned long long vload64(const unsigned long long *p) {
+  return *(const volatile unsigned long long *)p;
+}
+
+// Takes ticket (sweep, t) of slice sl if one is open and at most one round ahead.
+__device__ bool take_ticket(SliceCtx *ctx, const JacobiParams &p, int sl, int &sweep, int &t) {
+  SliceCtx &c = ctx[sl];
+  if (vload(&c.finished)) return false;
+  const int cols = p.desc ? p.desc[sl].cols : p.cols;
+  const int nb = tc_blocks(cols), np = nb / 2;
+  const unsigned total = (unsigned)(np * (nb - 1));
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const unsigned long long sn = vload64(&c.sn);
+    const int w = (int)(sn >> 32);
+    const unsigned tk = (unsigned)sn;
+    if (w == 0 || tk >= total) return false;
+    if ((int)(tk / np) > vload(&c.done) / np + 1) return false;
+    if (atomicCAS(&c.sn, sn, sn + 1) == sn) {
+      sweep = w;
+      t = (int)tk;
+      return true;
+    }
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiParams p) {
   constexpr int W2 = SmemTc::W2;
-  constexpr int B = W2 / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t tmem_base;
   // the swizzled operand tiles need 1024-byte alignment (the launch adds the slack)
@@ -1037,6 +1101,11 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
   SmemTc &s = groups[g];
   const GroupBar gbar{1 + g};
   const double tol = p.tol;
+  SchedHdr *hdr = reinterpret_cast<SchedHdr *>(p.sched);
+  SliceCtx *ctx = reinterpret_cast<SliceCtx *>(hdr + 1);
+  const int nbmax = tc_blocks(p.max_cols);
+  int *ver = reinterpret_cast<int *>(ctx + p.nslices);
+  float *snap = reinterpret_cast<float *>(ver + (int64_t)p.nslices * nbmax);
   if (tid == 0) {
     for (int b = 0; b < 3; ++b) tc::mbar_init(&s.bar[b], 1);
     tc::mbar_init_fence();
@@ -1049,75 +1118,162 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
   if (tid == 0) s.tmem = tmem_base + 64u * (uint32_t)g;
   gbar.sync();
 
-  const bool shared_slice = gps > 1;
-  const int lead = shared_slice ? g : 0;          // index of this group among its slice's
-  const int nlead = shared_slice ? TC_GROUPS : 1;
-  SmemTc &s0 = shared_slice ? groups[0] : s;      // holds the slice index
   uint32_t phase = 0;
-  for (int iter = 0;; ++iter) {
-    const int par = iter & 1;
-    if (lead == 0 && tid == 0) s0.slice[par] = atomicAdd(p.queue, 1);
-    if (shared_slice) __syncthreads(); else gbar.sync();
-    const int slice = s0.slice[par];
-    if (slice >= p.nslices) break;
-    const SliceView<float> v = slice_view<float>(p, slice);
-    int nb = (v.cols + B - 1) / B;
-    if (nb & 1) ++nb;
-    if (nb < 2) nb = 2;
-    for (int c = lead; c < v.cols; c += nlead)      // V = I
-      for (int r = tid; r < v.cols; r += NT)
-        __stcg(v.V + (int64_t)c * v.cols + r, r == c ? 1.f : 0.f);
+  int cur = -1;                        // slice this worker prefers (tid 0's view)
+  bool queue_open = true;
+  int cache_slice = -1, cache_sweep = 0;   // column order held in s.ord
+  const int worker = blockIdx.x * TC_GROUPS + g;
+  for (;;) {
+    // ---- tid 0 finds the next work item and broadcasts it
     if (tid == 0) {
+      int kind = WK_EXIT, sl = -1, w = 0, t = 0;
+      for (unsigned idle = 0;; ++idle) {
+        if (vload(&hdr->abort)) break;
+        if (cur >= 0 && take_ticket(ctx, p, cur, w, t)) {
+          kind = WK_PAIR;
+          sl = cur;
+          break;
+        }
+        if (queue_open) {
+          const int n = atomicAdd(p.queue, 1);
+          if (n < p.nslices) {
+            kind = WK_START;
+            sl = n;
+            break;
+          }
+          queue_open = false;
+        }
+        const int started = min(vload(p.queue), p.nslices);
+        bool got = false;
+        for (int k = 0; k < started && !got; ++k) {
+          const int cand = (worker + k) % started;
+          if (take_ticket(ctx, p, cand, w, t)) {
+            got = true;
+            sl = cand;
+          }
+        }
+        if (got) {
+          kind = WK_PAIR;
+          cur = sl;
+          break;
+        }
+        if (vload(&hdr->fin) >= p.nslices) break;
+        if (idle >= SCHED_SPIN) {
+          atomicExch(&hdr->abort, 1);
+          s.fail = 1;
+          break;
+        }
+        __nanosleep(1000);
+      }
+      __threadfence();                 // what the ticket's publisher wrote is visible
+      s.wk[0] = kind;
+      s.wk[1] = sl;
+      s.wk[2] = w;
+      s.wk[3] = t;
+    }
+    gbar.sync();
+    const int kind = s.wk[0], slice = s.wk[1], sweep = s.wk[2], ticket = s.wk[3];
+    if (kind == WK_EXIT) break;
+    const SliceView<float> v = slice_view<float>(p, slice);
+    if (kind == WK_START) {
+      // V = I, then open sweep 1
+      for (int c = 0; c < v.cols; ++c)
+        for (int r = tid; r < v.cols; r += NT)
+          __stcg(v.V + (int64_t)c * v.cols + r, r == c ? 1.f : 0.f);
+      __threadfence();
+      gbar.sync();
+      if (tid == 0) {
+        cur = slice;
+        atomicExch(&ctx[slice].sn, 1ull << 32);
+      }
+      continue;
+    }
+    // ---- one block pair of slice `slice`, sweep `sweep`
+    SliceCtx &c = ctx[slice];
+    const int nb = tc_blocks(v.cols), np = nb / 2;
+    const int round = ticket / np, q = ticket % np;
+    int bi, bj;
+    rr_pair(nb, round, q, bi, bj);
+    const bool sorted = v.nrm2 != nullptr && v.cols <= MAXSORT;
+    if (sorted && (cache_slice != slice || cache_sweep != sweep)) {
+      sort_columns(s, snap + (int64_t)slice * p.max_cols, v.cols, sweep == 1, tid, gbar);
+      cache_slice = slice;
+      cache_sweep = sweep;
+    }
+    if (tid == 0) {
+      // both blocks must have finished the previous round
+      const int need = (sweep - 1) * (nb - 1) + round;
+      const int *vi = ver + (int64_t)slice * nbmax + bi, *vj = ver + (int64_t)slice * nbmax + bj;
+      for (unsigned it = 0; vload(vi) < need || vload(vj) < need; ++it) {
+        if (vload(&hdr->abort)) break;
+        if (it >= SCHED_SPIN) {
+          atomicExch(&hdr->abort, 1);
+          s.fail = 1;
+          break;
+        }
+        __nanosleep(256);
+      }
+      __threadfence();
       s.nrot = 0;
       s.nonfinite = 0;
     }
-    if (shared_slice) __syncthreads(); else gbar.sync();
-
-    const bool sorted = v.nrm2 != nullptr && v.cols <= MAXSORT;
-    int converged = 0, sweep = 0;
-    for (sweep = 1; sweep <= p.max_sweeps; ++sweep) {
-      if (tid == 0) s.sweep_any = 0;
-      if (sorted) sort_columns(s, v.nrm2, v.cols, sweep == 1, tid, gbar);
-      for (int round = 0; round < nb - 1; ++round) {
-        for (int q = lead; q < nb / 2; q += nlead) {
-          int bi, bj;
-          rr_pair(nb, round, q, bi, bj);
-          pair_columns<W2>(s, bi, bj, v.cols, sorted, tid);
-          gbar.sync();
-          gram_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
-          for (int is = 0; is < p.inner_sweeps; ++is) {
-            inner_sweep<float, W2, 2>(s, tol, round == 0, is == 0, tid, gbar);
-            if (!s.step_rot) break;
-          }
-          gbar.sync();
-          if (sorted && tid < W2 && s.col[tid] >= 0)     // squared norms after this step
-            __stcg(v.nrm2 + s.col[tid], s.G[s.gcur][tri<W2>(tid, tid)]);
-          if (s.any_rot) {
-            if (tid == 0) s.sweep_any = 1;
-            build_bq(s, tid, gbar);
-            apply_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
-            apply_tc(s, v.V, v.cols, v.cols, phase, tid, gbar);
-          }
-          gbar.sync();
-        }
-        if (shared_slice) {
-          __threadfence();
-          __syncthreads();
-        }
-      }
-      // did any group of this slice rotate during the sweep?
-      const int any = shared_slice ? __syncthreads_or(s.sweep_any) : gbar.sync_or(s.sweep_any);
-      if (!any) {
-        converged = 1;
-        break;
-      }
+    pair_columns<W2>(s, bi, bj, v.cols, sorted, tid);
+    gbar.sync();
+    gram_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
+    for (int is = 0; is < p.inner_sweeps; ++is) {
+      inner_sweep<float, W2, 2>(s, tol, round == 0, is == 0, tid, gbar);
+      if (!s.step_rot) break;
     }
+    gbar.sync();
+    if (sorted && tid < W2 && s.col[tid] >= 0)     // squared norms after this step
+      __stcg(v.nrm2 + s.col[tid], s.G[s.gcur][tri<W2>(tid, tid)]);
+    if (s.any_rot) {
+      build_bq(s, tid, gbar);
+      apply_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
+      apply_tc(s, v.V, v.cols, v.cols, phase, tid, gbar);
+    }
+    __threadfence();
+    gbar.sync();
     if (tid == 0) {
-      atomicAdd((unsigned long long *)&p.rots[slice], (unsigned long long)s.nrot);
+      const int rotated = s.any_rot;
+      if (s.nrot) atomicAdd((unsigned long long *)&p.rots[slice], (unsigned long long)s.nrot);
       if (s.nonfinite) atomicOr(p.status, ST_NONFINITE);
-      if (lead == 0) {
-        p.sweeps[slice] = converged ? sweep : -1;
-        if (!converged) atomicOr(p.status, ST_NOCONV);
+      if (rotated) atomicOr(&c.rot[sweep & 1], 1);
+      __threadfence();
+      atomicAdd(ver + (int64_t)slice * nbmax + bi, 1);
+      atomicAdd(ver + (int64_t)slice * nbmax + bj, 1);
+      const int d = atomicAdd(&c.done, 1) + 1;
+      int reopen = 0;
+      if (d == np * (nb - 1)) {
+        // last pair of the sweep: close it
+        __threadfence();
+        const int any = vload(&c.rot[sweep & 1]);
+        if (!any || sweep >= p.max_sweeps) {
+          p.sweeps[slice] = any ? -1 : sweep;
+          if (any) atomicOr(p.status, ST_NOCONV);
+          c.finished = 1;
+          __threadfence();
+          atomicAdd(&hdr->fin, 1);
+        } else {
+          reopen = 1;
+        }
+      }
+      s.reopen = reopen;
+    }
+    gbar.sync();
+    if (s.reopen) {
+      // the next sweep: snapshot of the norms this sweep left, then its tickets
+      if (sorted) {
+        float *sn = snap + (int64_t)slice * p.max_cols;
+        for (int k = tid; k < v.cols; k += NT) __stcg(sn + k, __ldcg(v.nrm2 + k));
+      }
+      __threadfence();
+      gbar.sync();
+      if (tid == 0) {
+        c.rot[(sweep + 1) & 1] = 0;
+        c.done = 0;
+        __threadfence();
+        atomicExch(&c.sn, (unsigned long long)(sweep + 1) << 32);
       }
     }
   }
@@ -1171,11 +1327,16 @@ cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hi
   return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-// gps_hint: groups per slice (1 or TC_GROUPS; 0 = one group per slice when there are at
-// least two slices per SM, else the CTA's groups share a slice); grid_hint: CTAs.
-cudaError_t launch_jacobi_tc(const JacobiParams &p, cudaStream_t st, int gps_hint,
-                             int grid_hint) {
+size_t sched_bytes_for(int64_t nslices, int64_t max_cols) {
+  return sizeof(SchedHdr) + (size_t)nslices * sizeof(SliceCtx) +
+         (size_t)nslices * (size_t)tc_blocks((int)max_cols) * sizeof(int) +
+         (size_t)nslices * (size_t)max_cols * sizeof(float);
+}
+
+// grid_hint: CTAs (0 = one per SM).  The scheduler state is zeroed here, in stream order.
+cudaError_t launch_jacobi_tc(const JacobiParams &p, cudaStream_t st, int grid_hint) {
   static_assert(TC_GROUPS * sizeof(SmemTc) + 1024 <= 227 * 1024, "shared memory of a CTA");
+  if (p.sched == nullptr || p.nslices < 1) return cudaErrorInvalidValue;
   const size_t smem = (size_t)TC_GROUPS * sizeof(SmemTc) + 1024;
   cudaError_t e = cudaFuncSetAttribute(jacobi_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1188,14 +1349,11 @@ cudaError_t launch_jacobi_tc(const JacobiParams &p, cudaStream_t st, int gps_hin
                                                      smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  int gps = gps_hint == 1 || gps_hint == TC_GROUPS
-                ? gps_hint
-                : (p.nslices >= 2 * sms ? 1 : TC_GROUPS);
-  // every SM (one group per slice: fewer busy groups per SM run faster than packed ones)
-  int grid = grid_hint > 0 ? grid_hint : sms * per_sm;
-  if (grid > p.nslices) grid = p.nslices;
-  if (grid < 1) grid = 1;
-  jacobi_tc_kernel<<<grid, NT * TC_GROUPS, smem, st>>>(p, gps);
+  // every CTA resident at once (workers wait on one another through global memory)
+  int grid = sms * per_sm;
+  if (grid_hint > 0 && grid_hint < grid) grid = grid_hint;
+  if ((e = cudaMemsetAsync(p.sched, 0, p.sched_bytes, st)) != cudaSuccess) return e;
+  jacobi_tc_kernel<<<grid, NT * TC_GROUPS, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -1362,6 +1520,10 @@ __global__ void transpose_kernel(const T *__restrict__ A, int64_t m, int64_t p, 
 
 }  // namespace
 
+size_t jacobi_sched_bytes(int64_t nslices, int64_t max_cols) {
+  return sched_bytes_for(nslices, max_cols);
+}
+
 template <typename T>
 cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, int cluster_hint,
                        int grid_hint, int stages) {
@@ -1370,7 +1532,7 @@ cudaError_t jacobi_run(const JacobiParams &p, cudaStream_t st, int width_hint, i
     // the automatic choice; any width when asked for explicitly)
     if (p.engine == JACOBI_TC || (p.engine == JACOBI_AUTO && p.cols >= 64 &&
                                   (width_hint == 0 || width_hint == 64)))
-      return launch_jacobi_tc(p, st, cluster_hint, grid_hint);
+      return launch_jacobi_tc(p, st, grid_hint);
   }
   int w = width_hint;
   if (w != 16 && w != 32 && w != 64) w = p.cols <= 8 ? 16 : (p.cols <= 16 || p.cols < 256 ? 32 : 64);
