@@ -650,22 +650,52 @@ __device__ __forceinline__ void put_chunk(unsigned char *tile, uint32_t row, uin
 // (K); a chunk's tile holds H (rows 0..63, one per column) over L (rows 64..127), so one
 // MMA with A = the whole tile (M = 128) and B = its first 64 rows (N = 64) accumulates
 // [H^T H ; L^T H] in TMEM.  Then G = H^T H + L^T H + (L^T H)^T, summed in that order.
-// Two tiles alternate; the loads of chunk ck+1 are in flight while chunk ck is stored.
+// Two tiles alternate.  Each thread copies its own 8 rows of a column GRING - 1 chunks
+// ahead (cp.async into a private slot of a ring in the G / Q area, dead until the
+// epilogue), so it needs no barrier to read them back; unaligned columns load directly.
+constexpr int GRING = 4;
 __device__ void gram_tc(SmemTc &s, const float *__restrict__ Wsl, int rows, int lda,
                         uint32_t &phase, int tid, const GroupBar &bar) {
   constexpr int W2 = SmemTc::W2;
   constexpr int GK = 32;
+  static_assert(GRING * W2 * GK * sizeof(float) <= sizeof(SmemTc::bq), "Gram ring");
   const int c = tid >> 2, q = tid & 3;             // column, 8-row quarter of the chunk
   const bool vec = (lda & 3) == 0 && ((uintptr_t)Wsl & 15) == 0;
   const int gc = s.col[c];
   const float *src = gc >= 0 ? Wsl + (int64_t)gc * lda : nullptr;
   const int nck = (rows + GK - 1) / GK;
   const uint32_t idesc = tc::instr_desc(2, 128, W2);
-  float v[8], vn[8];
-  load8(src, q * 8, rows, vec, v);
+  float *ring = reinterpret_cast<float *>(s.bq) + c * GK + q * 8;   // + slot * W2 * GK
+  // one commit group per chunk (empty past the end), so wait_group counts chunks
+  auto stage = [&](int ck) {
+    if (vec && ck < nck) {
+      const int r = ck * GK + q * 8;
+      int valid = rows - r;
+      valid = valid < 0 ? 0 : (valid > 8 ? 8 : valid);
+      const float *g0 = src != nullptr && valid > 0 ? src + r : Wsl;
+      const int b0 = src != nullptr ? (valid > 4 ? 4 : valid) * 4 : 0;
+      const int b1 = src != nullptr ? (valid > 4 ? valid - 4 : 0) * 4 : 0;
+      float *dst = ring + (ck % GRING) * (W2 * GK);
+      cp_async16(dst, g0, b0);
+      cp_async16(dst + 4, b1 > 0 ? g0 + 4 : g0, b1);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < GRING - 1; ++k) stage(k);
+  float v[8];
   for (int ck = 0; ck < nck; ++ck) {
     const int b = ck & 1;
-    if (ck + 1 < nck) load8(src, (ck + 1) * GK + q * 8, rows, vec, vn);
+    stage(ck + GRING - 1);
+    if (vec) {
+      cp_async_wait<GRING - 1>();
+      const float4 a0 = *reinterpret_cast<const float4 *>(ring + (ck % GRING) * (W2 * GK));
+      const float4 a1 = *reinterpret_cast<const float4 *>(ring + (ck % GRING) * (W2 * GK) + 4);
+      v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w;
+      v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
+    } else {
+      load8(src, ck * GK + q * 8, rows, false, v);
+    }
     if (ck >= 2) tc_wait(s, b, phase);             // the MMAs of chunk ck-2 read tile b
     unsigned char *tile = s.op + b * 16384;
     uint32_t h[8], l[8];
@@ -689,9 +719,8 @@ __device__ void gram_tc(SmemTc &s, const float *__restrict__ Wsl, int rows, int 
       }
       tc::mma_commit(&s.bar[b]);
     }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = vn[e];
   }
+  cp_async_wait<0>();                              // the ring area becomes G below
   for (int ck = nck >= 2 ? nck - 2 : 0; ck < nck; ++ck) tc_wait(s, ck & 1, phase);
   tc::fence_after_sync();
   // epilogue: warps 2, 3 park L^T H (TMEM lanes 64..127) in the tile area, XOR-swizzled
