@@ -36,6 +36,8 @@ WORKLOADS = {
     # name: (shape, eps, description)
     "climate": ((1024, 512, 365), 1e-2,
                 "t-SVDM-II climate-shaped 1024x512x365 FP32, DCT-II, eps=1e-2"),
+    "climate-304": ((1024, 512, 304), 1e-2,
+                    "t-SVDM-II climate-shaped 1024x512x304 FP32, DCT-II, eps=1e-2"),
     "climate-128": ((1024, 512, 128), 1e-2,
                     "t-SVDM-II climate-shaped 1024x512x128 FP32, DCT-II, eps=1e-2"),
     "climate-medium": ((1024, 512, 48), 1e-2,
@@ -130,7 +132,7 @@ def jacobi_traffic_per_slice():
     """DRAM bytes per slice of the Jacobi kernel from the committed ncu summary, or None
     when the kernel source changed since those counters were taken."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "jacobi_kernel_climate_1024x512x128.md")
+    prof = os.path.join(ROOT, "profiles", "jacobi_tc_kernel_climate_1024x512x304.md")
     src = os.path.join(ROOT, "paper_2605_16058_gb300", "csrc", "jacobi.cu")
     try:
         txt = open(prof).read()
@@ -475,8 +477,12 @@ def main():
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": (None if jacobi_traffic_per_slice() is None
                                  else jacobi_traffic_per_slice() * n3),
-                     "traffic_note": "ncu dram bytes per slice (1024x512x128 capture) x slices",
+                     "traffic_note": "ncu dram bytes per slice (1024x512x304 capture) x slices",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "note": "classical one-sided Jacobi flop count (3 m p (p-1) per sweep + "
+                             "6 (m + p) per rotation) against the FP32 CUDA-core peak; the "
+                             "Gram and rotation apply run as split products on tcgen05, the "
+                             "inner Gram sweeps on the CUDA cores",
                      "algorithmic_flops": alg_flops, "kernel_ms": jac_ms},
         "stages_ms": stages,
         "ttm_roofline": {"bound": "hbm", "achieved": ttm_gbs, "peak": pk["hbm_gbs"],
