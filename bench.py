@@ -254,7 +254,7 @@ def run_batch_bench(args, world, rank, local):
                      "kernel_ms": choice["jacobi_ms"],
                      "algorithmic_flops": alg_flops,
                      "achieved": alg_flops / (choice["jacobi_ms"] * 1e-3) / 1e12},
-        "clocks": clocks, "gpu_launches": None,
+        "clocks": clocks, "gpu_launches": N.tsvdm_batch_graph_kernels(b) * args.steps,
     }
     line["roofline"]["frac"] = line["roofline"]["achieved"] / fp32_peak
     N.tsvdm_batch_destroy(b)

@@ -300,6 +300,9 @@ tsvdm_status tsvdm_batch_tune(tsvdm_batch b, const tsvdm_batch_io *io, int *choi
 /* Synchronises; sweeps and rotations summed over all slices of the last run, and the
  * device-detected status (ENOCONV, ENONFINITE, ETIMEOUT or OK, then cleared). */
 tsvdm_status tsvdm_batch_status(tsvdm_batch b, int64_t *sweeps, int64_t *rotations);
+/* Kernel launches in one replay of the captured graph (its kernel nodes), in *kernels.
+ * EINVAL before tsvdm_batch_capture. */
+tsvdm_status tsvdm_batch_graph_kernels(tsvdm_batch b, int64_t *kernels);
 
 /* Allocation-free t-SVDM-II rank choice.  The paper has no counterpart: it exists for
  * callers that must not call cudaMalloc (a process whose device memory is all handed to

@@ -439,6 +439,22 @@ tsvdm_status tsvdm_batch_status(tsvdm_batch b, int64_t *sweeps, int64_t *rotatio
   return TSVDM_OK;
 }
 
+tsvdm_status tsvdm_batch_graph_kernels(tsvdm_batch b, int64_t *kernels) {
+  if (!b || !kernels || !b->graph) return TSVDM_EINVAL;
+  size_t n = 0;
+  CKB(cudaGraphGetNodes(b->graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) CKB(cudaGraphGetNodes(b->graph, nodes.data(), &n));
+  int64_t k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    CKB(cudaGraphNodeGetType(nodes[i], &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *kernels = k;
+  return TSVDM_OK;
+}
+
 tsvdm_status tsvdm_batch_tune(tsvdm_batch b, const tsvdm_batch_io *io, int *choice) {
   if (!b || !io) return TSVDM_EINVAL;
   struct Cand { int width, cluster, stages, engine; };

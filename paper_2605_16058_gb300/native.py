@@ -50,6 +50,7 @@ SIGNATURES = {
     "tsvdm_batch_launch": (_i32, [_vp]),
     "tsvdm_batch_tune": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
     "tsvdm_batch_status": (_i32, [_vp, _pi64, _pi64]),
+    "tsvdm_batch_graph_kernels": (_i32, [_vp, _pi64]),
     "tsvdm_select_ranks_noalloc": (_i32, [_vp, _i64, _i64, _dbl, _vp, _vp, _vp, _vp]),
     "tsvdm_adam": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _i64, _dbl, _dbl, _dbl, _dbl, _vp]),
 }
@@ -250,6 +251,12 @@ def tsvdm_batch_status(b):
     a, c = ctypes.c_int64(0), ctypes.c_int64(0)
     st = lib().tsvdm_batch_status(b, ctypes.byref(a), ctypes.byref(c))
     return st, a.value, c.value
+
+
+def tsvdm_batch_graph_kernels(b):
+    k = ctypes.c_int64(0)
+    check(lib().tsvdm_batch_graph_kernels(b, ctypes.byref(k)), "tsvdm_batch_graph_kernels")
+    return k.value
 
 
 def tsvdm_batch_destroy(b):

@@ -107,6 +107,7 @@ def test_batch_run_graph_replay_and_autotuner(prec):
         for t in keep:                                   # wipe the outputs, replay the graph
             t["S"].zero_(); t["U"].zero_(); t["rel"].zero_()
         N.tsvdm_batch_capture(b, ios)
+        assert N.tsvdm_batch_graph_kernels(b) >= len(keep) + 4   # TTMs, Jacobi, selection, ...
         for t in keep:
             t["S"].zero_(); t["U"].zero_(); t["rel"].zero_()
         torch.cuda.synchronize()
@@ -132,6 +133,9 @@ def test_batch_capture_needs_a_non_default_stream():
     try:
         with pytest.raises(N.TsvdmError) as e:
             N.tsvdm_batch_capture(b, ios[:1])
+        assert e.value.status == N.EINVAL
+        with pytest.raises(N.TsvdmError) as e:            # nothing captured
+            N.tsvdm_batch_graph_kernels(b)
         assert e.value.status == N.EINVAL
     finally:
         N.tsvdm_batch_destroy(b)
