@@ -1063,10 +1063,11 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
 // (the stopping rule of the scalar method), else it copies the squared column norms the
 // sweep left into a per-slice snapshot and opens the next sweep's tickets (every worker
 // sorts the sweep's column order from the snapshot, so all agree on the blocks while the
-// sweep's own pairs keep updating the norms).  A worker takes a
-// ticket from its current slice, else starts a new slice, else helps any open slice; a
-// ticket more than one round ahead of the completed ones is left to others.  Every wait is
-// bounded; on expiry the kernel raises a global abort flag and ST_TIMEOUT.
+// sweep's own pairs keep updating the norms).  A worker takes the next ticket of its
+// current slice, else starts a new slice, else helps any open slice, and only takes a
+// ticket whose two blocks are already free (the pair then runs without waiting; the
+// earliest unfinished ticket always becomes free).  Every wait is bounded; on expiry the
+// kernel raises a global abort flag and ST_TIMEOUT.
 constexpr int TC_GROUPS = 3;
 constexpr uint32_t TC_COLS = 256;     // TMEM columns of the CTA (64 per group, power of two)
 constexpr unsigned SCHED_SPIN = 1u << 24;   // polls of a dependency or idle wait (~1 us each)
@@ -1097,8 +1098,10 @@ __device__ __forceinline__ unsigned long long vload64(const unsigned long long *
   return *(const volatile unsigned long long *)p;
 }
 
-// Takes ticket (sweep, t) of slice sl if one is open and at most one round ahead.
-__device__ bool take_ticket(SliceCtx *ctx, const JacobiParams &p, int sl, int &sweep, int &t) {
+// Takes ticket (sweep, t) of slice sl if one is open and its two blocks are already free
+// (so that the worker does not wait; the earliest unfinished ticket always becomes free).
+__device__ bool take_ticket(SliceCtx *ctx, const int *ver, int nbmax, const JacobiParams &p,
+                            int sl, int &sweep, int &t) {
   SliceCtx &c = ctx[sl];
   if (vload(&c.finished)) return false;
   const int cols = p.desc ? p.desc[sl].cols : p.cols;
@@ -1109,7 +1112,14 @@ __device__ bool take_ticket(SliceCtx *ctx, const JacobiParams &p, int sl, int &s
     const int w = (int)(sn >> 32);
     const unsigned tk = (unsigned)sn;
     if (w == 0 || tk >= total) return false;
-    if ((int)(tk / np) > vload(&c.done) / np + 1) return false;
+    {
+      const int round = (int)(tk / np), q = (int)(tk % np);
+      int bi, bj;
+      rr_pair(nb, round, q, bi, bj);
+      const int need = (w - 1) * (nb - 1) + round;
+      const int *v = ver + (int64_t)sl * nbmax;
+      if (vload(v + bi) < need || vload(v + bj) < need) return false;
+    }
     if (atomicCAS(&c.sn, sn, sn + 1) == sn) {
       sweep = w;
       t = (int)tk;
@@ -1158,7 +1168,7 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
       int kind = WK_EXIT, sl = -1, w = 0, t = 0;
       for (unsigned idle = 0;; ++idle) {
         if (vload(&hdr->abort)) break;
-        if (cur >= 0 && take_ticket(ctx, p, cur, w, t)) {
+        if (cur >= 0 && take_ticket(ctx, ver, nbmax, p, cur, w, t)) {
           kind = WK_PAIR;
           sl = cur;
           break;
@@ -1176,7 +1186,7 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
         bool got = false;
         for (int k = 0; k < started && !got; ++k) {
           const int cand = (worker + k) % started;
-          if (take_ticket(ctx, p, cand, w, t)) {
+          if (take_ticket(ctx, ver, nbmax, p, cand, w, t)) {
             got = true;
             sl = cand;
           }
