@@ -452,6 +452,26 @@ def main():
                "h2d_bytes_per_step": in_bytes + n3 * n3 * 4, "d2h_bytes_per_step": int(d2h),
                "ms_per_step": te * 1e3}
 
+    # back-transform of the packed t-SVDM-II factors to the original domain (per-slice
+    # U S V^T, then x3 M^{-1}): CUDA events around the C-ABI call on the plan's stream.
+    # Algorithmic bytes: the factors read once, the n1 x n2 x n3 result written once.
+    native.tsvdm_plan_profile(plan.handle, 0)
+    Xk = torch.empty_like(X)
+    plan.reconstruct(U, S, V, M, offsets=offs, out=Xk)
+    torch.cuda.synchronize()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(3):
+        plan.reconstruct(U, S, V, M, offsets=offs, out=Xk)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rec_ms = r0.elapsed_time(r1) / 3
+    rec_bytes = (int(tot) * (n1 + n2 + 1) + n1 * n2 * n3 + n3 * n3) * 4
+    rec_rel = float(((Xk - X).pow(2).sum(dtype=torch.float64) /
+                     X.pow(2).sum(dtype=torch.float64)).sqrt())
+    del Xk
+
     # roofline of the dominant kernel (batched Jacobi), live CUDA-event duration
     jac_ms = statistics.mean(s["jacobi"] for s in stage_ms)
     m_, p_ = max(n1, n2), min(n1, n2)
@@ -491,6 +511,14 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": e2e,
+        "reconstruct": {"ms": rec_ms, "rel_err": rec_rel,
+                        "slice_product_flops": 2.0 * n1 * n2 * int(tot),
+                        "roofline": {"bound": "hbm",
+                                     "achieved": rec_bytes / (rec_ms * 1e-3) / 1e9,
+                                     "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                     "frac": rec_bytes / (rec_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                                     "algorithmic_bytes": rec_bytes,
+                                     "peak_source": "of %s" % src}},
     }
     if not args.no_learned:
         # fwd+bwd of the learned Cayley transform: crystal-shaped 512x256x128 FP32, k = 16,

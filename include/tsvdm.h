@@ -125,6 +125,9 @@ tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster
  *                      slice); under tsvdm_plan_set_tuning, clusters caps the CTAs
  *                      launched, cluster_size and stages are ignored.
  * AUTO uses TC for F32 slices of at least 64 columns unless block_width asks for 16 or 32.
+ * The engine also selects how tsvdm_reconstruct and tsvdm_backward form the slice
+ * products U_i diag(S_i) V_i^T of F32 plans: tensor cores (AUTO, TC; three-term BF16
+ * split, FP32-level accuracy) or FMA.
  * ENOTSUP for TC on an F64 plan, EINVAL for other values. */
 typedef enum {
   TSVDM_JACOBI_AUTO = 0,

@@ -324,13 +324,27 @@ tsvdm_status pack_impl(tsvdm_plan_s *p, void *U, void *S, void *V) {
   return TSVDM_OK;
 }
 
+// Out_i (+)= U_i diag(S_i) V_i^T: tensor cores for FP32 plans unless the FMA engine was
+// chosen (tsvdm_plan_set_engine), CUDA cores otherwise.
+template <typename T>
+cudaError_t products(tsvdm_plan_s *p, const T *U, const T *S, const T *V,
+                     const int64_t *offsets, int64_t k, int64_t n3, T *Out, bool subtract,
+                     double *sumsq) {
+  if constexpr (sizeof(T) == 4) {
+    if (p->engine != JACOBI_FMA)
+      return slice_products_tc(U, S, V, offsets, k, p->n1, p->n2, n3, Out, subtract, sumsq,
+                               p->status, p->st);
+  }
+  return slice_products<T>(U, S, V, offsets, k, p->n1, p->n2, n3, Out, subtract, sumsq, p->st);
+}
+
 template <typename T>
 tsvdm_status reconstruct_impl(tsvdm_plan_s *p, const void *U, const void *S, const void *V,
                               const int64_t *offsets, int64_t k, const void *M, void *Xk) {
   p->tol_valid = 0;
   stage_begin(p, TSVDM_STAGE_OTHER);
-  CK(slice_products<T>((const T *)U, (const T *)S, (const T *)V, offsets, k, p->n1, p->n2, p->n3,
-                       (T *)p->Ahat, false, nullptr, p->st));
+  CK(products<T>(p, (const T *)U, (const T *)S, (const T *)V, offsets, k, p->n3,
+                 (T *)p->Ahat, false, nullptr));
   stage_end(p, TSVDM_STAGE_OTHER, 1);
   return run_ttm<T>(p, (const T *)p->Ahat, p->n1 * p->n2, (const T *)M, true, (T *)Xk, nullptr);
 }
@@ -346,8 +360,8 @@ tsvdm_status backward_impl(tsvdm_plan_s *p, const void *X, const void *M, int64_
                               p->scal + SC_XNORM2);
   if (s != TSVDM_OK) return s;
   stage_begin(p, TSVDM_STAGE_OTHER);
-  CK(slice_products<T>((const T *)U, (const T *)S, (const T *)V, nullptr, k, p->n1, p->n2, n,
-                       (T *)p->Ahat, true, p->scal + SC_E, p->st));
+  CK(products<T>(p, (const T *)U, (const T *)S, (const T *)V, nullptr, k, n, (T *)p->Ahat,
+                 true, p->scal + SC_E));
   CK(backward_scalars(p->scal, dL, p->st));
   stage_end(p, TSVDM_STAGE_OTHER, 2);
   if (dX) {

@@ -134,6 +134,12 @@ template <typename T>
 cudaError_t slice_products(const T *U, const T *S, const T *V, const int64_t *offsets,
                            int64_t k, int64_t n1, int64_t n2, int64_t n3, T *Out,
                            bool subtract_from_out, double *sumsq, cudaStream_t st);
+// The same product for FP32 factors on the tensor cores (three-term BF16 split, FP32-level
+// accuracy); a bounded wait that runs out sets ST_TIMEOUT in *status.
+cudaError_t slice_products_tc(const float *U, const float *S, const float *V,
+                              const int64_t *offsets, int64_t k, int64_t n1, int64_t n2,
+                              int64_t n3, float *Out, bool subtract_from_out, double *sumsq,
+                              int *status, cudaStream_t st);
 
 // C (n x n) = alpha * A^T B with A, B column-major P x n; split over P; alpha from device.
 template <typename T>

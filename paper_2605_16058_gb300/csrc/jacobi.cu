@@ -762,20 +762,9 @@ __device__ void gram_tc(SmemTc &s, const float *__restrict__ Wsl, int rows, int 
 // sweeps), so it splits every value into three BF16 terms x = x1 + x2 + x3 (each the
 // rounding of what the previous ones leave; |x - x1 - x2 - x3| <= 2^-27 |x|) and forms the
 // six products whose order is at least 2^-24: x1 y1, x1 y2, x2 y1, x1 y3, x3 y1, x2 y2.
-__device__ __forceinline__ void split3(float x, __nv_bfloat16 &a, __nv_bfloat16 &b,
-                                       __nv_bfloat16 &c) {
-  a = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r1);
-  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
-}
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-// 16-byte chunk `ch` (8 BF16 values) of row `row` of a K-major 64-byte-swizzled tile.
-__device__ __forceinline__ uint32_t sw64(uint32_t row, uint32_t ch) {
-  return row * 64 + ((ch ^ ((row >> 1) & 3)) << 4);
-}
+using tc::pack2;
+using tc::split3;
+using tc::sw64;
 
 constexpr uint32_t AP_TERM = 8192;    // one term of the apply's A tile: [128 rows x 32 K] BF16
 constexpr uint32_t BQ_TERM = 8192;    // one term of (Q - I): 2 K-blocks x [64 x 32] BF16

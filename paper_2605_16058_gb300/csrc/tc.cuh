@@ -4,6 +4,8 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 namespace tsvdm {
 namespace tc {
 
@@ -124,6 +126,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
   for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
+// Three-term BF16 split x = x1 + x2 + x3 (each the rounding of what the previous ones
+// leave; |x - x1 - x2 - x3| <= 2^-27 |x|).  With the six products of order >= 2^-24
+// (x1 y1, x1 y2, x2 y1, x1 y3, x3 y1, x2 y2) a BF16 MMA reaches FP32-level products.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &a, __nv_bfloat16 &b,
+                                       __nv_bfloat16 &c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+// Byte offset of 16-byte chunk `ch` (8 BF16 values) of row `row` of a K-major tile with
+// 64-byte rows and 64-byte swizzle.
+__device__ __forceinline__ uint32_t sw64(uint32_t row, uint32_t ch) {
+  return row * 64 + ((ch ^ ((row >> 1) & 3)) << 4);
+}
 // TF32 rounding (round to nearest, ties away), kept in an FP32 container.
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t v;

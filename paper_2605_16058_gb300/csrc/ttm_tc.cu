@@ -10,14 +10,17 @@
 //           D += A_hi B_hi + A_hi B_lo + A_lo B_hi  (three kind::f16 MMAs per k-step)
 //   TF32    D += A B with both operands rounded to TF32 (one kind::tf32 MMA per k-step)
 //
-// Warp roles (256 threads):
-//   warp 0      TMA producer: raw FP32 X tile (128 rows x 32 t, no swizzle) and the
-//               pre-converted K-major B tiles (swizzled) of each stage;
-//   warp 1      TMEM allocation; one thread issues the MMAs and commits them;
-//   warps 4..7  converters (thread = row): FP32 X -> K-major swizzled operand tiles,
-//               then the epilogue (tcgen05.ld of its own TMEM lane -> scale -> store).
+// Persistent: one CTA per SM (a kernel that holds tensor memory runs one CTA per SM)
+// loops over row tiles; the stage ring runs across tiles.  Warp roles (384 threads):
+//   warp 0       TMA producer: raw FP32 X tile (128 rows x 32 t, no swizzle) and the
+//                pre-converted K-major B tiles (swizzled) of each stage;
+//   warp 1       TMEM allocation; one thread issues the MMAs and commits them (a tile's
+//                first MMA waits until the epilogue has read the previous accumulator);
+//   warps 4..7   converters (thread = row): FP32 X -> K-major swizzled operand tiles;
+//   warps 8..11  epilogue (tcgen05.ld of its own TMEM lane -> scale -> store), which
+//                overlaps the next tile's loads and conversions.
 // Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT in the status
-// word and runs to completion (TMEM is always released).  Nothing traps.
+// word, every role leaves its loop and TMEM is released.  Nothing traps.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -31,7 +34,7 @@ namespace {
 constexpr int TBM = 128;
 constexpr int TBK = 32;
 constexpr int MAX_STAGES = 4;
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 384;   // warps 0 TMA, 1 MMA + TMEM, 4-7 converters, 8-11 epilogue
 constexpr unsigned SPIN_LIMIT = 1u << 26;
 
 struct TcParams {
@@ -110,16 +113,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t *full = (uint64_t *)(smem + STAGES * L.stage);
   uint64_t *conv = full + MAX_STAGES;
   uint64_t *empty = conv + MAX_STAGES;
-  uint64_t *done = empty + MAX_STAGES;
-  uint32_t *tmem_slot = (uint32_t *)(done + 1);
+  uint64_t *tfull = empty + MAX_STAGES;        // a tile's accumulator is complete
+  uint64_t *tempty = tfull + 1;                // the epilogue has read it (TMEM free)
+  uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // the halves of one row tile are adjacent blocks, so the second reads X from L2
-  const int64_t m0 = (int64_t)blockIdx.y * TBM;
-  const int n_base = blockIdx.x * p.nsub;          // first output column of this CTA
+  const int n_base = blockIdx.y * p.nsub;      // first output column of this CTA
   const bool bf = p.prec == TSVDM_P_BF16X3;
   const int nk = p.kt_count;
+  const int ntiles = (int)((p.P + TBM - 1) / TBM);
 
   if (tid == 0) {
     s_fail = 0;
@@ -128,7 +131,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 128);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -142,23 +146,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // bounded wait; after the first expiry every role stops waiting and leaves its loop
+  auto wait = [&](uint64_t *bar, uint32_t par) -> bool {
+    if (*(volatile int *)&s_fail) return false;
+    if (!mbar_wait(bar, par)) {
+      s_fail = 1;
+      return false;
+    }
+    return true;
+  };
 
+  // Persistent: CTA b takes row tiles b, b + gridDim.x, ...; the stage ring runs across
+  // tiles (iteration it = tiles before x nk + kt), so the TMA and the converters fill the
+  // next tile's stages while the epilogue warps drain the accumulator of the last one.
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
+    // ---------------- TMA producer: raw FP32 X tile + pre-split K-major B tiles
     const uint32_t bytes = TBK * TBM * 4 + L.b_bytes;
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES, u = kt / STAGES;
-      if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) { s_fail = 1; break; }
-      unsigned char *st = smem + s * L.stage;
-      mbar_expect_tx(&full[s], bytes);
-      tma_load_2d(st + L.raw, &mapX, &full[s], (int)m0, kt * TBK);
-      // B: [ops][npad rows][32 K]; box rows <= 256
-      const int ops = bf ? 2 : 1;
-      const uint32_t row_bytes = bf ? 64 : 128;
-      for (int o = 0; o < ops; ++o)
-        for (int r0 = 0; r0 < p.nsub; r0 += p.box_rows)
-          tma_load_2d(st + L.b + (uint32_t)o * p.nsub * row_bytes + (uint32_t)r0 * row_bytes,
-                      &mapB, &full[s], kt * TBK, o * p.npad + n_base + r0);
+    const int ops = bf ? 2 : 1;
+    const uint32_t row_bytes = bf ? 64 : 128;
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const int m0 = tile * TBM;
+      for (int kt = 0; kt < nk; ++kt, ++it) {
+        const int s = it % STAGES, u = it / STAGES;
+        if (u > 0 && !wait(&empty[s], (u - 1) & 1)) { ok = false; break; }
+        unsigned char *st = smem + s * L.stage;
+        mbar_expect_tx(&full[s], bytes);
+        tma_load_2d(st + L.raw, &mapX, &full[s], m0, kt * TBK);
+        for (int o = 0; o < ops; ++o)
+          for (int r0 = 0; r0 < p.nsub; r0 += p.box_rows)
+            tma_load_2d(st + L.b + (uint32_t)o * p.nsub * row_bytes + (uint32_t)r0 * row_bytes,
+                        &mapB, &full[s], kt * TBK, o * p.npad + n_base + r0);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -167,121 +187,137 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t lay = bf ? 4u : 2u;
     const uint32_t row_bytes = bf ? 64u : 128u;
     const int ksub = bf ? TBK / 16 : TBK / 8;
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES, u = kt / STAGES;
-      if (!mbar_wait(&conv[s], u & 1)) { s_fail = 1; break; }
+    int it = 0, j = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++j) {
+      if (j > 0 && !wait(tempty, (j - 1) & 1)) break;      // accumulator drained
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      unsigned char *st = smem + s * L.stage;
-      for (int kk = 0; kk < ksub; ++kk) {
-        const uint32_t koff = kk * 32;                      // 32 bytes per k-step
-        for (int n0 = 0; n0 < p.nsub; n0 += 256) {
-          const uint32_t nn = (p.nsub - n0) < 256 ? (uint32_t)(p.nsub - n0) : 256u;
-          const uint32_t idesc = instr_desc(fmt, nn);
-          const uint32_t d = tmem + (uint32_t)n0;
-          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-          if (bf) {
-            uint64_t ahi = smem_desc(st + L.a + koff, sbo, lay);
-            uint64_t alo = smem_desc(st + L.a + TBM * 64 + koff, sbo, lay);
-            uint64_t bhi = smem_desc(st + L.b + n0 * row_bytes + koff, sbo, lay);
-            uint64_t blo = smem_desc(st + L.b + (uint32_t)p.nsub * row_bytes + n0 * row_bytes + koff,
-                                     sbo, lay);
-            mma_f16(d, ahi, bhi, idesc, acc);
-            mma_f16(d, ahi, blo, idesc, 1u);
-            mma_f16(d, alo, bhi, idesc, 1u);
-          } else {
-            uint64_t a = smem_desc(st + L.a + koff, sbo, lay);
-            uint64_t b = smem_desc(st + L.b + n0 * row_bytes + koff, sbo, lay);
-            mma_tf32(d, a, b, idesc, acc);
+      for (int kt = 0; kt < nk; ++kt, ++it) {
+        const int s = it % STAGES, u = it / STAGES;
+        if (!wait(&conv[s], u & 1)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char *st = smem + s * L.stage;
+        for (int kk = 0; kk < ksub; ++kk) {
+          const uint32_t koff = kk * 32;                    // 32 bytes per k-step
+          for (int n0 = 0; n0 < p.nsub; n0 += 256) {
+            const uint32_t nn = (p.nsub - n0) < 256 ? (uint32_t)(p.nsub - n0) : 256u;
+            const uint32_t idesc = instr_desc(fmt, nn);
+            const uint32_t d = tmem + (uint32_t)n0;
+            const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            if (bf) {
+              uint64_t ahi = smem_desc(st + L.a + koff, sbo, lay);
+              uint64_t alo = smem_desc(st + L.a + TBM * 64 + koff, sbo, lay);
+              uint64_t bhi = smem_desc(st + L.b + n0 * row_bytes + koff, sbo, lay);
+              uint64_t blo = smem_desc(st + L.b + (uint32_t)p.nsub * row_bytes + n0 * row_bytes + koff,
+                                       sbo, lay);
+              mma_f16(d, ahi, bhi, idesc, acc);
+              mma_f16(d, ahi, blo, idesc, 1u);
+              mma_f16(d, alo, bhi, idesc, 1u);
+            } else {
+              uint64_t a = smem_desc(st + L.a + koff, sbo, lay);
+              uint64_t b = smem_desc(st + L.b + n0 * row_bytes + koff, sbo, lay);
+              mma_tf32(d, a, b, idesc, acc);
+            }
           }
         }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&empty[s]);
+      if (ok) mma_commit(tfull);
     }
-    mma_commit(done);
-  } else if (warp >= 4) {
-    // ---------------- converters, then epilogue
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- converters (thread = row): FP32 X -> K-major swizzled operands
     const int row = tid - 128;
     double ss = 0.0;
     const bool do_ss = p.sumsq != nullptr;
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES, u = kt / STAGES;
-      if (!mbar_wait(&full[s], u & 1)) { s_fail = 1; break; }
-      unsigned char *st = smem + s * L.stage;
-      const float *raw = (const float *)(st + L.raw);
-      float x[TBK];
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int kt = 0; kt < nk; ++kt, ++it) {
+        const int s = it % STAGES, u = it / STAGES;
+        if (!wait(&full[s], u & 1)) { ok = false; break; }
+        unsigned char *st = smem + s * L.stage;
+        const float *raw = (const float *)(st + L.raw);
+        float x[TBK];
 #pragma unroll
-      for (int k = 0; k < TBK; ++k) x[k] = raw[k * TBM + row];
-      if (do_ss) {
+        for (int k = 0; k < TBK; ++k) x[k] = raw[k * TBM + row];
+        if (do_ss) {
 #pragma unroll
-        for (int k = 0; k < TBK; ++k) ss += (double)x[k] * (double)x[k];
-      }
-      if (bf) {
-        unsigned char *ahi = st + L.a, *alo = st + L.a + TBM * 64;
+          for (int k = 0; k < TBK; ++k) ss += (double)x[k] * (double)x[k];
+        }
+        if (bf) {
+          unsigned char *ahi = st + L.a, *alo = st + L.a + TBM * 64;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint32_t h[4], l[4];
+          for (int c = 0; c < 4; ++c) {
+            uint32_t h[4], l[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            float x0 = x[c * 8 + 2 * q], x1 = x[c * 8 + 2 * q + 1];
-            __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-            __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-            __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-            h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            for (int q = 0; q < 4; ++q) {
+              float x0 = x[c * 8 + 2 * q], x1 = x[c * 8 + 2 * q + 1];
+              __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+              __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+              __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+              h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+              l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            const uint32_t off = (uint32_t)row * 64 + (((uint32_t)c ^ (((uint32_t)row >> 1) & 3)) << 4);
+            *(uint4 *)(ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *(uint4 *)(alo + off) = make_uint4(l[0], l[1], l[2], l[3]);
           }
-          const uint32_t off = (uint32_t)row * 64 + (((uint32_t)c ^ (((uint32_t)row >> 1) & 3)) << 4);
-          *(uint4 *)(ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-          *(uint4 *)(alo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-      } else {
-        unsigned char *a = st + L.a;
+        } else {
+          unsigned char *a = st + L.a;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          uint32_t v[4];
+          for (int c = 0; c < 8; ++c) {
+            uint32_t v[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v[q]) : "f"(x[c * 4 + q]));
-          const uint32_t off = (uint32_t)row * 128 + (((uint32_t)c ^ ((uint32_t)row & 7)) << 4);
-          *(uint4 *)(a + off) = make_uint4(v[0], v[1], v[2], v[3]);
+            for (int q = 0; q < 4; ++q)
+              asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v[q]) : "f"(x[c * 4 + q]));
+            const uint32_t off = (uint32_t)row * 128 + (((uint32_t)c ^ ((uint32_t)row & 7)) << 4);
+            *(uint4 *)(a + off) = make_uint4(v[0], v[1], v[2], v[3]);
+          }
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv[s]);
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&conv[s]);
     }
     if (do_ss) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       if (lane == 0) atomicAdd(p.sumsq, ss);
     }
-    // epilogue
-    const bool ok = mbar_wait(done, 0);
-    if (!ok) s_fail = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  } else if (warp >= 8) {
+    // ---------------- epilogue (thread = TMEM lane = row): scale, optional beta Z, store
+    const int row = tid - 256;
+    const uint32_t lane_base = (uint32_t)(32 * (warp - 8)) << 16;
     const float scale = p.scale_ptr ? (float)(*p.scale_ptr) : 1.f;
     const float beta = p.beta_ptr ? (float)(*p.beta_ptr) : 0.f;
-    const int64_t grow = m0 + row;
-    const uint32_t lane_base = (uint32_t)(32 * (warp - 4)) << 16;
-    for (int j0 = 0; j0 < p.nsub; j0 += 16) {
-      uint32_t v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-          "%11, %12, %13, %14, %15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(tmem + lane_base + (uint32_t)j0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (ok && grow < p.P) {
+    int j = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+      if (!wait(tfull, j & 1)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t grow = (int64_t)tile * TBM + row;
+      for (int j0 = 0; j0 < p.nsub; j0 += 16) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+            "%11, %12, %13, %14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + lane_base + (uint32_t)j0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (grow < p.P) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int64_t col = n_base + j0 + e;
-          if (col < p.J) {
-            float y = scale * __uint_as_float(v[e]);
-            if (p.Z) y = fmaf(beta, p.Z[grow + p.P * col], y);
-            p.Y[grow + p.P * col] = y;
+          for (int e = 0; e < 16; ++e) {
+            const int64_t col = n_base + j0 + e;
+            if (col < p.J) {
+              float y = scale * __uint_as_float(v[e]);
+              if (p.Z) y = fmaf(beta, p.Z[grow + p.P * col], y);
+              p.Y[grow + p.P * col] = y;
+            }
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(tempty);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -412,19 +448,22 @@ cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t
   uint32_t cols = 32;
   while (cols < (uint32_t)nsub) cols <<= 1;
   p.tmem_cols = cols;
-  // two CTAs per SM with two stages when they fit, else the deepest pipeline that fits
-  int stages = 2;
-  if (2 * (tc_layout(nsub, prec, 2).total + 1024) > 227 * 1024) {
-    stages = MAX_STAGES;
-    while (stages > 2 && tc_layout(nsub, prec, stages).total + 1024 > 227 * 1024) --stages;
-  }
+  // the deepest pipeline that fits (one CTA per SM)
+  int stages = MAX_STAGES;
+  while (stages > 2 && tc_layout(nsub, prec, stages).total + 1024 > 227 * 1024) --stages;
   p.stages = stages;
   const TcLayout L = tc_layout(nsub, prec, stages);
   const size_t smem = L.total + 1024;
   cudaError_t e = cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)nsplit, (unsigned)((P + TBM - 1) / TBM));
+  // persistent: one CTA per SM (a kernel holding tensor memory runs one CTA per SM)
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  const int64_t ntiles = (P + TBM - 1) / TBM;
+  const dim3 grid((unsigned)(ntiles < sms ? ntiles : sms), (unsigned)nsplit);
   ttm_tc_kernel<<<grid, TC_THREADS, smem, st>>>(mapX, mapB, p);
   return cudaGetLastError();
 }

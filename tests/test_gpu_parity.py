@@ -174,6 +174,37 @@ def test_reconstruct_matches_oracle(dt):
     assert abs(direct - out["rel_err"]) <= (2e-5 if dt == torch.float32 else 1e-11)
 
 
+@pytest.mark.parametrize("engine", ["tc", "fma"])
+@pytest.mark.parametrize("flat", [False, True])
+def test_reconstruct_packed_each_engine(engine, flat):
+    """Back-transform of packed t-SVDM-II factors (ranks vary per slice) over several
+    128 x 256 output tiles with ragged edges, both engines of the slice products, against
+    the oracle's reconstruction of the same factors.  flat: X nearly constant along mode 3,
+    so the DCT leaves almost all energy in slice 0 and the other slices get rank 0."""
+    rng = np.random.default_rng(17)
+    n1, n2, n3 = 300, 270, 4
+    if flat:
+        A = synth.cp_tensor(n1, n2, 1, 40, rng, noise_rel=1e-2)[:, :, 0]
+        X = A[:, :, None] * np.ones(n3) + 1e-6 * rng.standard_normal((n1, n2, n3))
+    else:
+        X = synth.cp_tensor(n1, n2, n3, 40, rng, noise_rel=1e-2)
+    X = X.astype(np.float32).astype(np.float64)
+    M = synth.dct2_matrix(n3).astype(np.float32).astype(np.float64)
+    plan = _plan(n1, n2, n3, torch.float32)
+    plan.set_engine(engine)
+    Md = t_lib(M, dtype=torch.float32)
+    out = plan.tolerance(t_lib(X, dtype=torch.float32), Md, 0.05)
+    ranks = out["ranks"].cpu().numpy()
+    if flat:
+        assert ranks[0] > 0 and (ranks[1:] == 0).all()
+    offs = out["offsets"]
+    Xk = np_lib(plan.reconstruct(out["U"], out["S"], out["V"], Md, offsets=offs))
+    want = oracle.reconstruct(np_lib(out["U"]), np_lib(out["S"]), np_lib(out["V"]), M.T,
+                              offsets=offs.cpu().numpy())
+    assert np.max(np.abs(Xk - want)) <= 1e-5 * np.max(np.abs(want))
+    assert abs(oracle.rel_err_direct(X, Xk) - out["rel_err"]) <= 2e-5
+
+
 def test_original_domain_factors():
     X, M = _case_input("tall", (60, 30, 6))
     n1, n2, n3 = X.shape
