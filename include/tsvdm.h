@@ -92,6 +92,24 @@ tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype d
                                tsvdm_plan *out);
 tsvdm_status tsvdm_plan_destroy(tsvdm_plan plan);
 
+/* Plans for d-way tensors, 3 <= d <= TSVDM_MAX_ORDER (the order-d star-M product of
+ * Sec. 2.1 applied to every mode k >= 3; the paper's higher-order layouts such as a 6-way
+ * reanalysis tensor).  X is n_1 x n_2 x ... x n_d, column-major (n_1 fastest); the transform
+ * is Ahat = X x_3 M_3 x_4 M_4 ... x_d M_d, and the slice SVDs run over all N = n_3 ... n_d
+ * trailing index combinations (slice index i_3 + n_3 i_4 + n_3 n_4 i_5 + ...).  On such a
+ * plan every entry point's M argument is the concatenation of M_3, M_4, ..., M_d (each
+ * n_k x n_k column-major, stored one after the other; for inverse transforms and
+ * reconstruction the same matrices on an orthogonal plan, else their inverses), and the
+ * factors are laid out as for a 3-way tensor with n3 = N (U n_1 x k x N, S k x N,
+ * V n_2 x k x N; packed t-SVDM-II factors likewise).  m_is_orthogonal declares every M_k a
+ * nonzero multiple of an orthogonal matrix.  tsvdm_backward returns ENOTSUP on a d-way
+ * plan with d > 3; the batch API is 3-way.  d = 3 gives an ordinary plan.  EINVAL for d
+ * outside [3, TSVDM_MAX_ORDER] or non-positive dims. */
+#define TSVDM_MAX_ORDER 8
+tsvdm_status tsvdm_plan_create_dway(int d, const int64_t *dims, tsvdm_dtype dtype,
+                                    tsvdm_prec prec, int m_is_orthogonal, void *stream,
+                                    tsvdm_plan *out);
+
 /* Jacobi controls.  tol is the relative off-diagonal threshold
  * |a_i^T a_j| <= tol ||a_i|| ||a_j|| under which a column pair counts as orthogonal
  * (<= 0 restores the default: 4 sqrt(m) u with u the unit roundoff of the dtype);

@@ -23,7 +23,10 @@ Readings of the paper used here (where it is silent or ambiguous):
   * the truncation loss used for differentiation is the transform-domain relative error
     sqrt(sum of discarded sigma^2) / ||X||_F, equal to the original-domain error when M
     is orthogonal (Sec. 2.3);
-  * the Cayley form of an orthogonal M is M(A) = (I+W)^{-1}(I-W) M0 with W = A^T - A.
+  * the Cayley form of an orthogonal M is M(A) = (I+W)^{-1}(I-W) M0 with W = A^T - A;
+  * a d-way tensor (d > 3) takes one matrix M_k along every mode k >= 3 (the order-d star-M
+    product of Sec. 2.1); its frontal slices are all trailing index combinations, in
+    column-major order (i3 fastest), and t-SVDM-I/II treat them as one set of slices.
 
 Parity unpinned: the paper's compression-ratio and error values on its real datasets
 (NCEP/NCAR reanalysis, NekRS Taylor-Green vortex, MoVO2 X-ray volume) cannot be pinned,
@@ -144,9 +147,48 @@ def svd_slices(Ahat, max_sweeps=MAX_SWEEPS, threads=None):
     return U, S, V, sweeps
 
 
+def ttm_mode(X, M, mode):
+    """Y = X x_mode M for a d-way X (Sec. 2.1's mode-k product; mode is 0-based):
+    Y(.., i, ..) = sum_t M[i,t] X(.., t, ..).  Each trailing index combination is one
+    mode-3 product of the (leading dims) x 1 x n_mode view, done by ttm3's loops."""
+    X = _f64(X)
+    M = _f64(M)
+    shp = X.shape
+    lead = int(np.prod(shp[:mode], dtype=np.int64))
+    tail = int(np.prod(shp[mode + 1:], dtype=np.int64))
+    X3 = X.reshape((lead, shp[mode], tail), order="F")
+    Y3 = np.empty((lead, M.shape[0], tail), order="F")
+    for q in range(tail):
+        Y3[:, :, q] = ttm3(np.asfortranarray(X3[:, None, :, q]), M)[:, 0, :]
+    return Y3.reshape(shp[:mode] + (M.shape[0],) + shp[mode + 1:], order="F")
+
+
+def dway_transform(X, Ms):
+    """Ahat = X x_3 M_3 x_4 M_4 ... for a d-way X and the list Ms = [M_3, M_4, ...]."""
+    Y = _f64(X)
+    for j, M in enumerate(Ms):
+        Y = ttm_mode(Y, M, 2 + j)
+    return Y
+
+
+def to_slices(Y):
+    """n1 x n2 x n3 x ... x nd -> n1 x n2 x (n3 ... nd), slice index i3 + n3 i4 + ..."""
+    return Y.reshape((Y.shape[0], Y.shape[1], -1), order="F")
+
+
+def _transform(X, M):
+    """The forward transform of Algorithm 1: ttm3 for a 3-way X and one M; for a d-way X
+    and a list of matrices (one per mode >= 3), all of them, viewed as frontal slices."""
+    if isinstance(M, (list, tuple)):
+        return to_slices(dway_transform(X, M))
+    return ttm3(X, M)
+
+
 def full_tsvdm(X, M, threads=None, max_sweeps=MAX_SWEEPS):
-    """Algorithm 1: Ahat = X x_3 M, then the thin SVD of every frontal slice of Ahat."""
-    Ahat = ttm3(X, M)
+    """Algorithm 1: Ahat = X x_3 M, then the thin SVD of every frontal slice of Ahat.  For a
+    d-way X, M is the list of per-mode matrices and the slices run over all trailing index
+    combinations."""
+    Ahat = _transform(X, M)
     U, S, V, sweeps = svd_slices(Ahat, max_sweeps=max_sweeps, threads=threads)
     return dict(Ahat=Ahat, U=U, S=S, V=V, sweeps=sweeps)
 
@@ -245,7 +287,16 @@ def reconstruct(U, S, V, Minv, k=None, offsets=None):
     """X_k = (U_i diag(S_i) V_i^T per slice) x_3 M^{-1}.
 
     Uniform rank: U (m,k,n), S (k,n), V (p,k,n).  Variable rank: packed U (m,total),
-    S (total,), V (p,total) with ``offsets`` (n+1)."""
+    S (total,), V (p,total) with ``offsets`` (n+1).  For a d-way tensor Minv is the list of
+    per-mode inverses [M_3^{-1}, M_4^{-1}, ...] and the result is m x p x n3 x ... x nd."""
+    if isinstance(Minv, (list, tuple)):
+        dims = tuple(_f64(Mi).shape[0] for Mi in Minv)
+        eye = np.eye(int(np.prod(dims)))
+        Ak = reconstruct(U, S, V, eye, k=k, offsets=offsets)        # slice products only
+        Ak = Ak.reshape(Ak.shape[:2] + dims, order="F")
+        for j, Mi in enumerate(Minv):
+            Ak = ttm_mode(Ak, Mi, 2 + j)
+        return Ak
     Minv = _f64(Minv)
     n = Minv.shape[0]
     if offsets is None:
@@ -277,8 +328,17 @@ def rel_err_direct(X, Xk) -> float:
 
 
 def original_domain(F, Minv):
-    """Map a hat-domain factor (m x k x n) or diagonal block (k x n) back by M^{-1}."""
+    """Map a hat-domain factor (m x k x n) or diagonal block (k x n) back by M^{-1} (for a
+    d-way tensor: the list of per-mode inverses, n = n3 ... nd slices)."""
     F = np.asarray(F, dtype=np.float64)
+    if isinstance(Minv, (list, tuple)):
+        dims = tuple(_f64(Mi).shape[0] for Mi in Minv)
+        G = F[:, None, :] if F.ndim == 2 else F
+        G = G.reshape(G.shape[:2] + dims, order="F")
+        for j, Mi in enumerate(Minv):
+            G = ttm_mode(G, Mi, 2 + j)
+        G = to_slices(G)
+        return G[:, 0, :] if F.ndim == 2 else G
     if F.ndim == 2:
         return ttm3(F[:, None, :], Minv)[:, 0, :]
     return ttm3(F, Minv)

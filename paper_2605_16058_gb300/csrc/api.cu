@@ -40,6 +40,11 @@ struct tsvdm_plan_s {
   int max_sweeps = 40;
   int width_hint = 0, cluster_hint = 0, grid_hint = 0, stages_hint = 0, inner_sweeps = 2;
   int engine = JACOBI_AUTO;
+  // d-way tensors: the trailing modes (dims td[0..dw-1], n3 = their product), one matrix
+  // per mode, concatenated in the M buffer at element offsets mo[]; dw = 0: 3-way plan
+  int dw = 0;
+  int64_t td[TSVDM_MAX_ORDER] = {}, mo[TSVDM_MAX_ORDER] = {}, msum = 0;
+  void *dtmp = nullptr;      // ping-pong buffer of the per-mode TTMs (n1 n2 n3 elements)
   int tol_valid = 0;
   int64_t tol_total = 0;
   void *stage[STG_COUNT] = {};
@@ -146,9 +151,64 @@ cudaError_t ttm_any(tsvdm_plan_s *p, const T *X, int64_t P, const T *M, bool tra
   return ttm_simt<T>(X, P, n, M, n, n, transB, Y, scale, beta, Z, sumsq, p->st);
 }
 
+// Elements of the transform argument: n3^2, or the concatenated per-mode matrices.
+int64_t m_elems(const tsvdm_plan_s *p) { return p->dw ? p->msum : p->n3 * p->n3; }
+
+// Y = X x_3 M (or M^{-1}) on a (P x n) column-major view, n explicit.
+template <typename T>
+cudaError_t ttm_n(tsvdm_plan_s *p, const T *X, int64_t P, int64_t n, const T *M, bool transB,
+                  T *Y, const double *scale) {
+  if constexpr (sizeof(T) == 4) {
+    if ((p->prec == TSVDM_P_TF32 || p->prec == TSVDM_P_BF16X3) && p->tc_ws &&
+        ttm_tc_supported(P, n, n, X, Y))
+      return ttm_tc((const float *)X, P, n, (const float *)M, n, transB, (int)p->prec, (float *)Y,
+                    p->tc_ws, p->tc_ws_bytes, nullptr, scale, nullptr, nullptr, p->status, p->st);
+  }
+  return ttm_simt<T>(X, P, n, M, n, n, transB, Y, scale, nullptr, nullptr, nullptr, p->st);
+}
+
+// d-way: Y = X x_3 M_3 x_4 M_4 ... (or the inverses) for a tensor of P0 x td[0] x td[1] x ...
+// (P0 = n1 n2 for the data, n1 k / n2 k / k for factors).  The mode-(3+m) product is a
+// batch over the trailing index q of (P_m x td[m]) mode-3 products, P_m = P0 prod_{i<m}
+// td[i]; the modes commute.  Results ping-pong between Y and the plan's buffer so that the
+// last mode lands in Y (X is never written).
+template <typename T>
+tsvdm_status transform_dway(tsvdm_plan_s *p, const T *X, int64_t P0, const T *M, bool inverse,
+                            T *Y) {
+  const int d = p->dw;
+  int nl = 0;
+  stage_begin(p, TSVDM_STAGE_TTM);
+  int64_t Pm = P0;
+  const T *src = X;
+  for (int m = 0; m < d; ++m) {
+    const int64_t nm = p->td[m];
+    int64_t Qm = 1;
+    for (int i = m + 1; i < d; ++i) Qm *= p->td[i];
+    T *dst = ((d - 1 - m) % 2 == 0) ? Y : (T *)p->dtmp;
+    const T *Mm = M + p->mo[m];
+    const double *scale = nullptr;
+    bool transB = false;
+    if (inverse && p->ortho) {
+      CK(inv_scale<T>(Mm, nm, p->scal + SC_INVSCALE, p->st));
+      scale = p->scal + SC_INVSCALE;
+      transB = true;
+      ++nl;
+    }
+    for (int64_t q = 0; q < Qm; ++q) {
+      CK(ttm_n<T>(p, src + q * Pm * nm, Pm, nm, Mm, transB, dst + q * Pm * nm, scale));
+      nl += (p->prec == TSVDM_P_TF32 || p->prec == TSVDM_P_BF16X3) ? 2 : 1;
+    }
+    src = dst;
+    Pm *= nm;
+  }
+  stage_end(p, TSVDM_STAGE_TTM, nl);
+  return TSVDM_OK;
+}
+
 template <typename T>
 tsvdm_status run_ttm(tsvdm_plan_s *p, const T *X, int64_t P, const T *M, bool inverse, T *Y,
                      double *sumsq) {
+  if (p->dw) return transform_dway<T>(p, X, P, M, inverse, Y);
   const int64_t n = p->n3;
   stage_begin(p, TSVDM_STAGE_TTM);
   int nl = 1;
@@ -233,7 +293,7 @@ tsvdm_status fixed_rank_impl(tsvdm_plan_s *p, const void *X, const void *M, int6
   bool sX, sM, sU, sS, sV;
   tsvdm_status s;
   if ((s = stage_in(p, STG_X, X, e * n1 * n2 * n3, true, &dX, &sX)) != TSVDM_OK) return s;
-  if ((s = stage_in(p, STG_M, M, e * n3 * n3, true, &dM, &sM)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_M, M, e * m_elems(p), true, &dM, &sM)) != TSVDM_OK) return s;
   if ((s = stage_in(p, STG_U, U, e * n1 * k * n3, false, &dU, &sU)) != TSVDM_OK) return s;
   if ((s = stage_in(p, STG_S, S, e * k * n3, false, &dS, &sS)) != TSVDM_OK) return s;
   if ((s = stage_in(p, STG_V, V, e * n2 * k * n3, false, &dV, &sV)) != TSVDM_OK) return s;
@@ -279,7 +339,7 @@ tsvdm_status tolerance_impl(tsvdm_plan_s *p, const void *X, const void *M, doubl
   bool sX, sM;
   tsvdm_status s;
   if ((s = stage_in(p, STG_X, X, e * n1 * n2 * n3, true, &dX, &sX)) != TSVDM_OK) return s;
-  if ((s = stage_in(p, STG_M, M, e * n3 * n3, true, &dM, &sM)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_M, M, e * m_elems(p), true, &dM, &sM)) != TSVDM_OK) return s;
   if ((s = decompose<T>(p, (const T *)dX, (const T *)dM)) != TSVDM_OK) return s;
   stage_begin(p, TSVDM_STAGE_SELECT);
   CK(select_ranks<T>((const T *)p->sig, (int)p->cols, (int)n3, eps, p->keys, p->scal,
@@ -392,7 +452,7 @@ bool valid_plan(tsvdm_plan p) { return p != nullptr && p->Ahat != nullptr; }
 void free_plan(tsvdm_plan_s *p) {
   void *bufs[] = {p->Ahat, p->Wt, p->Vw, p->sig, p->keys, p->perm, p->sweeps, p->status,
                   p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk, p->tc_ws,
-                  p->norm2, p->sched};
+                  p->norm2, p->sched, p->dtmp};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < STG_COUNT; ++i)
@@ -490,6 +550,41 @@ tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype d
     cudaGetLastError();
     free_plan(p);
     return err == cudaErrorMemoryAllocation ? TSVDM_ENOMEM : TSVDM_ECUDA;
+  }
+  *out = p;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_create_dway(int d, const int64_t *dims, tsvdm_dtype dtype,
+                                    tsvdm_prec prec, int m_is_orthogonal, void *stream,
+                                    tsvdm_plan *out) {
+  if (!out || !dims) return TSVDM_EINVAL;
+  *out = nullptr;
+  if (d < 3 || d > TSVDM_MAX_ORDER) return TSVDM_EINVAL;
+  int64_t n3 = 1;
+  for (int i = 2; i < d; ++i) {
+    if (dims[i] <= 0 || dims[i] > (1 << 30)) return TSVDM_EINVAL;
+    if (n3 > ((int64_t)1 << 30) / dims[i]) return TSVDM_EINVAL;
+    n3 *= dims[i];
+  }
+  tsvdm_plan p = nullptr;
+  tsvdm_status s = tsvdm_plan_create(dims[0], dims[1], n3, dtype, prec, m_is_orthogonal, stream,
+                                     &p);
+  if (s != TSVDM_OK) return s;
+  if (d > 3) {
+    p->dw = d - 2;
+    int64_t off = 0;
+    for (int m = 0; m < p->dw; ++m) {
+      p->td[m] = dims[2 + m];
+      p->mo[m] = off;
+      off += dims[2 + m] * dims[2 + m];
+    }
+    p->msum = off;
+    if (cudaMalloc(&p->dtmp, p->esz * (size_t)p->n1 * p->n2 * n3) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(p);
+      return TSVDM_ENOMEM;
+    }
   }
   *out = p;
   return TSVDM_OK;
@@ -599,6 +694,7 @@ tsvdm_status tsvdm_backward(tsvdm_plan plan, const void *X, const void *M, int64
                             const void *U, const void *S, const void *V, double dL, void *dX,
                             void *dM, double *loss) {
   if (!valid_plan(plan) || !X || !M || !U || !S || !V) return TSVDM_EINVAL;
+  if (plan->dw) return TSVDM_ENOTSUP;
   begin_call(plan);
   if (k < 1 || k > plan->cols) return TSVDM_EINVAL;
   if (plan->dtype == TSVDM_F32)

@@ -27,6 +27,8 @@ _pi64, _pdbl = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "tsvdm_plan_create": (_i32, [_i64, _i64, _i64, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
     "tsvdm_plan_destroy": (_i32, [_vp]),
+    "tsvdm_plan_create_dway": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _vp,
+                                      ctypes.POINTER(_vp)]),
     "tsvdm_plan_set_jacobi": (_i32, [_vp, _dbl, _i32]),
     "tsvdm_plan_set_tuning": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
     "tsvdm_plan_set_engine": (_i32, [_vp, _i32]),
@@ -107,6 +109,15 @@ def tsvdm_plan_create(n1, n2, n3, dtype, prec, m_is_orthogonal, stream=None):
     h = ctypes.c_void_p()
     check(lib().tsvdm_plan_create(n1, n2, n3, dtype, prec, int(bool(m_is_orthogonal)),
                                   _stream(stream), ctypes.byref(h)), "tsvdm_plan_create")
+    return h
+
+
+def tsvdm_plan_create_dway(dims, dtype, prec, m_is_orthogonal, stream=None):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * max(len(dims), 1))(*[int(d) for d in dims])
+    check(lib().tsvdm_plan_create_dway(len(dims), arr, dtype, prec, int(bool(m_is_orthogonal)),
+                                       _stream(stream), ctypes.byref(h)),
+          "tsvdm_plan_create_dway")
     return h
 
 

@@ -42,6 +42,35 @@ class Plan:
         self.handle = N.tsvdm_plan_create(self.n1, self.n2, self.n3, _DT[dtype],
                                           N.PRECISIONS[prec], self.orthogonal, stream)
 
+    @classmethod
+    def dway(cls, dims, dtype=torch.float32, prec=None, orthogonal=True, stream=None,
+             device="cuda"):
+        """A plan for a d-way tensor of `dims` (n1, n2, n3, ..., nd): one transform matrix per
+        mode >= 3, passed to every method as one buffer holding M_3, M_4, ... one after the
+        other (see `concat`); the slices are the n3 ... nd trailing index combinations."""
+        self = cls.__new__(cls)
+        dims = [int(d) for d in dims]
+        self.n1, self.n2 = dims[0], dims[1]
+        self.n3 = 1
+        for d in dims[2:]:
+            self.n3 *= d
+        self.dims = tuple(dims)
+        self.dtype = dtype
+        self.device = torch.device(device)
+        if prec is None:
+            prec = "fp64" if dtype == torch.float64 else "fp32"
+        self.prec = prec
+        self.orthogonal = bool(orthogonal)
+        self.r = min(self.n1, self.n2)
+        self.handle = N.tsvdm_plan_create_dway(dims, _DT[dtype], N.PRECISIONS[prec],
+                                               self.orthogonal, stream)
+        return self
+
+    @staticmethod
+    def concat(mats):
+        """The per-mode matrices (library layout, i.e. torch tensors of to_lib) as one buffer."""
+        return torch.cat([m.reshape(-1) for m in mats])
+
     def close(self):
         if getattr(self, "handle", None) is not None:
             N.tsvdm_plan_destroy(self.handle)

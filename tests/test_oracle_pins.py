@@ -388,3 +388,78 @@ def test_rel_err_is_scale_free_for_multiples_of_orthogonal_m():
     assert abs(a["rel_err"] - b["rel_err"]) < 1e-13
     Xk = oracle.reconstruct(b["U"], b["S"], b["V"], c["M"].T / 3.0)
     assert abs(oracle.rel_err_direct(c["X"], Xk) - b["rel_err"]) < 1e-12
+
+
+# ---------------------------------------------------------------- d-way tensors
+def _dway_case(dims, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal(dims)
+    Ms = [synth.haar_orthogonal(n, rng) for n in dims[2:]]
+    return X, Ms
+
+
+def test_dway_transform_equals_kronecker_mode3():
+    """Modes 3 and 4 (and 5) transformed one after the other equal one mode-3 product of
+    the flattened trailing modes with the Kronecker product M_5 (x) M_4 (x) M_3 (column-major
+    flattening puts i3 fastest): a different computation of the same operator."""
+    for dims in [(5, 4, 3, 2), (4, 3, 2, 3, 2)]:
+        X, Ms = _dway_case(dims, 11)
+        K = Ms[0]
+        for M in Ms[1:]:
+            K = np.kron(M, K)
+        got = oracle.to_slices(oracle.dway_transform(X, Ms))
+        want = np.einsum("it,abt->abi", K, oracle.to_slices(X))
+        assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_dway_mode_product_against_einsum():
+    X, Ms = _dway_case((4, 3, 5, 2), 12)
+    got = oracle.ttm_mode(X, Ms[0], 2)
+    want = np.einsum("it,abtq->abiq", Ms[0], X)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+    got = oracle.ttm_mode(X, Ms[1], 3)
+    want = np.einsum("iq,abtq->abti", Ms[1], X)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_dway_with_trivial_last_mode_is_the_3way_decomposition():
+    X, Ms = _dway_case((12, 9, 5), 13)
+    X4 = X[:, :, :, None]
+    a = oracle.fixed_rank(X4, [Ms[0], np.ones((1, 1))], 4)
+    b = oracle.fixed_rank(X, Ms[0], 4)
+    assert np.max(np.abs(a["S"] - b["S"])) <= 1e-12 * b["S"].max()
+    assert abs(a["rel_err"] - b["rel_err"]) <= 1e-12
+
+
+def test_dway_eckart_young_and_reconstruction():
+    """Orthogonal M_k: the d-way transform is orthogonal, so the reported relative error
+    (discarded sigma^2) equals the direct reconstruction error, for t-SVDM-I and II."""
+    X, Ms = _dway_case((10, 8, 3, 4), 14)
+    Minv = [M.T for M in Ms]
+    f = oracle.fixed_rank(X, Ms, 3)
+    Xk = oracle.reconstruct(f["U"], f["S"], f["V"], Minv)
+    assert Xk.shape == X.shape
+    assert abs(oracle.rel_err_direct(X, Xk) - f["rel_err"]) <= 1e-12
+    t = oracle.tolerance(X, Ms, 0.3)
+    Xt = oracle.reconstruct(t["U"], t["S"], t["V"], Minv, offsets=t["offsets"])
+    assert abs(oracle.rel_err_direct(X, Xt) - t["rel_err"]) <= 1e-12
+    assert t["rel_err"] < 0.3
+    # full rank reproduces X
+    r = min(X.shape[:2])
+    g = oracle.fixed_rank(X, Ms, r)
+    Xr = oracle.reconstruct(g["U"], g["S"], g["V"], Minv)
+    assert oracle.rel_err_direct(X, Xr) <= 1e-12
+
+
+def test_dway_original_domain_factors_rebuild_x():
+    """Original-domain factors (each mapped back by the per-mode inverses) rebuild X_k with
+    the d-way star-M product, i.e. the transform of their facewise product."""
+    X, Ms = _dway_case((7, 6, 2, 3), 15)
+    Minv = [M.T for M in Ms]
+    f = oracle.fixed_rank(X, Ms, 6)
+    Xk = oracle.reconstruct(f["U"], f["S"], f["V"], Minv)
+    U = oracle.original_domain(f["U"], Minv)
+    # U x_3 M_3 x_4 M_4 returns the hat-domain factor
+    back = oracle.to_slices(oracle.dway_transform(U.reshape((7, 6, 2, 3), order="F"), Ms))
+    assert np.max(np.abs(back - f["U"])) <= 1e-13
+    assert oracle.rel_err_direct(X, Xk) <= 1e-12
