@@ -147,6 +147,19 @@ tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster
  * products U_i diag(S_i) V_i^T of F32 plans: tensor cores (AUTO, TC; three-term BF16
  * split, FP32-level accuracy) or FMA.
  * ENOTSUP for TC on an F64 plan, EINVAL for other values. */
+/* Warm start of the slice SVDs, for sequences of closely related tensors (learned-M
+ * training, where M changes by one optimiser step at a time; streaming data).  Once
+ * enabled, every decomposition after the first starts each slice's one-sided Jacobi from
+ * the previous decomposition's right vectors V_i: the slice becomes Ahat_i V_i (a slice
+ * product on the engine of tsvdm_plan_set_engine) and the rotations accumulate onto V_i,
+ * so a slice that changed little converges in a few sweeps.  The stopping rule and the
+ * outputs are those of a cold start (to the Jacobi tolerance; in FP32 the orthogonality of
+ * V can drift by ~1e-6 per call over long sequences).  Every call of this function makes
+ * the next decomposition start cold (call it again after a device-reported error);
+ * enable = 0 turns warm starts off.  The first enable allocates rows x cols x n3 elements
+ * of scratch (ENOMEM if that fails). */
+tsvdm_status tsvdm_plan_set_warm_start(tsvdm_plan plan, int enable);
+
 typedef enum {
   TSVDM_JACOBI_AUTO = 0,
   TSVDM_JACOBI_FMA = 1,

@@ -45,6 +45,9 @@ struct tsvdm_plan_s {
   int dw = 0;
   int64_t td[TSVDM_MAX_ORDER] = {}, mo[TSVDM_MAX_ORDER] = {}, msum = 0;
   void *dtmp = nullptr;      // ping-pong buffer of the per-mode TTMs (n1 n2 n3 elements)
+  // warm start of the slice SVDs: the next decomposition starts from the V in Vw
+  int warm = 0, warm_valid = 0;
+  void *warm_buf = nullptr;  // A_i V_i (rows cols n3 elements)
   int tol_valid = 0;
   int64_t tol_total = 0;
   void *stage[STG_COUNT] = {};
@@ -241,7 +244,18 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   }
   CK(cudaMemsetAsync(p->queue, 0, sizeof(int), p->st));
   CK(cudaMemsetAsync(p->rots, 0, sizeof(long long) * p->n3, p->st));
-  JacobiParams jp;
+  const bool warm = p->warm && p->warm_valid;
+  if (warm) {
+    // start from the previous right vectors: the slice becomes A_i V_i, V starts at V_i
+    stage_begin(p, TSVDM_STAGE_OTHER);
+    CK(slice_rotate<T>((const T *)work_matrix(p), (const T *)p->Vw, p->rows, p->cols, p->n3,
+                       (T *)p->warm_buf, sizeof(T) == 4 && p->engine != JACOBI_FMA, p->status,
+                       p->st));
+    CK(cudaMemcpyAsync(work_matrix(p), p->warm_buf, p->esz * p->rows * p->cols * p->n3,
+                       cudaMemcpyDeviceToDevice, p->st));
+    stage_end(p, TSVDM_STAGE_OTHER, 1);
+  }
+  JacobiParams jp{};
   jp.A = work_matrix(p);
   jp.V = p->Vw;
   jp.sA = p->rows * p->cols;
@@ -259,6 +273,7 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   jp.inner_sweeps = p->inner_sweeps;
   jp.desc = nullptr;
   jp.engine = p->engine;
+  jp.warm = warm ? 1 : 0;
   jp.sched = p->sched;
   jp.sched_bytes = p->sched_bytes;
   jp.max_cols = (int)p->cols;
@@ -269,6 +284,7 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   CK(jacobi_finalize<T>((const T *)work_matrix(p), jp.sA, jp.rows, jp.cols, jp.nslices,
                         (T *)p->sig, p->perm, p->st));
   stage_end(p, TSVDM_STAGE_FINALIZE, 1);
+  p->warm_valid = p->warm;           // Vw now holds every slice's right vectors
   return TSVDM_OK;
 }
 
@@ -452,7 +468,7 @@ bool valid_plan(tsvdm_plan p) { return p != nullptr && p->Ahat != nullptr; }
 void free_plan(tsvdm_plan_s *p) {
   void *bufs[] = {p->Ahat, p->Wt, p->Vw, p->sig, p->keys, p->perm, p->sweeps, p->status,
                   p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk, p->tc_ws,
-                  p->norm2, p->sched, p->dtmp};
+                  p->norm2, p->sched, p->dtmp, p->warm_buf};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < STG_COUNT; ++i)
@@ -629,6 +645,22 @@ tsvdm_status tsvdm_plan_set_engine(tsvdm_plan plan, int engine) {
   if (engine == TSVDM_JACOBI_TC && plan->dtype != TSVDM_F32) return TSVDM_ENOTSUP;
   plan->engine = engine == TSVDM_JACOBI_TC ? JACOBI_TC
                                            : (engine == TSVDM_JACOBI_FMA ? JACOBI_FMA : JACOBI_AUTO);
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_set_warm_start(tsvdm_plan plan, int enable) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  plan->warm_valid = 0;              // the next decomposition starts cold
+  plan->warm = 0;
+  if (!enable) return TSVDM_OK;
+  if (!plan->warm_buf &&
+      cudaMalloc(&plan->warm_buf, plan->esz * (size_t)plan->rows * plan->cols * plan->n3) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    plan->warm_buf = nullptr;
+    return TSVDM_ENOMEM;
+  }
+  plan->warm = 1;
   return TSVDM_OK;
 }
 

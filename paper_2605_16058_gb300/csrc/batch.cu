@@ -124,7 +124,7 @@ tsvdm_status run_batch(tsvdm_batch_s *b, const tsvdm_batch_io *io, bool timed) {
   }
   CKB(cudaMemsetAsync(b->queue, 0, sizeof(int), st));
   CKB(cudaMemsetAsync(b->rots, 0, sizeof(long long) * b->total_slices, st));
-  JacobiParams jp;
+  JacobiParams jp{};
   memset(&jp, 0, sizeof(jp));
   jp.rows = 0;
   jp.cols = b->min_cols;     // caps the cluster at the smallest slice's block pairs

@@ -83,6 +83,7 @@ struct JacobiParams {
   void *sched;         // tensor-core kernel's scheduler state (jacobi_sched_bytes), zeroed
   size_t sched_bytes;  //   by jacobi_run before the launch
   int max_cols;        // largest cols of any slice (sizes the scheduler state)
+  int warm;            // 1: V already holds the starting rotation (warm start), keep it
 };
 enum { JACOBI_AUTO = 0, JACOBI_FMA = 1, JACOBI_TC = 2 };
 
@@ -139,7 +140,13 @@ cudaError_t slice_products(const T *U, const T *S, const T *V, const int64_t *of
 cudaError_t slice_products_tc(const float *U, const float *S, const float *V,
                               const int64_t *offsets, int64_t k, int64_t n1, int64_t n2,
                               int64_t n3, float *Out, bool subtract_from_out, double *sumsq,
-                              int *status, cudaStream_t st);
+                              int *status, cudaStream_t st, bool vtrans = false);
+// Out_i = A_i V_i for column-major A_i (rows x cols) and V_i (cols x cols), slice strides
+// rows*cols and cols*cols (the warm start of the slice SVDs): the slice product with S = 1
+// and V read transposed.
+template <typename T>
+cudaError_t slice_rotate(const T *A, const T *V, int64_t rows, int64_t cols, int64_t n3, T *Out,
+                         bool tensor_cores, int *status, cudaStream_t st);
 
 // C (n x n) = alpha * A^T B with A, B column-major P x n; split over P; alpha from device.
 template <typename T>

@@ -973,10 +973,12 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
     if (nb & 1) ++nb;
     if (nb < 2) nb = 2;
 
-    // V = I (this CTA initialises columns crank, crank + csize, ...)
-    for (int c = crank; c < v.cols; c += csize)
-      for (int r = tid; r < v.cols; r += NT)
-        __stcg(v.V + (int64_t)c * v.cols + r, r == c ? T(1) : T(0));
+    // V = I (this CTA initialises columns crank, crank + csize, ...); a warm start keeps the
+    // caller's V (the slice then holds W V)
+    if (!p.warm)
+      for (int c = crank; c < v.cols; c += csize)
+        for (int r = tid; r < v.cols; r += NT)
+          __stcg(v.V + (int64_t)c * v.cols + r, r == c ? T(1) : T(0));
     if (tid == 0) {
       s.nrot = 0;
       s.nonfinite = 0;
@@ -1204,10 +1206,11 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
     if (kind == WK_EXIT) break;
     const SliceView<float> v = slice_view<float>(p, slice);
     if (kind == WK_START) {
-      // V = I, then open sweep 1
-      for (int c = 0; c < v.cols; ++c)
-        for (int r = tid; r < v.cols; r += NT)
-          __stcg(v.V + (int64_t)c * v.cols + r, r == c ? 1.f : 0.f);
+      // V = I (a warm start keeps the caller's V), then open sweep 1
+      if (!p.warm)
+        for (int c = 0; c < v.cols; ++c)
+          for (int r = tid; r < v.cols; r += NT)
+            __stcg(v.V + (int64_t)c * v.cols + r, r == c ? 1.f : 0.f);
       __threadfence();
       gbar.sync();
       if (tid == 0) {

@@ -18,7 +18,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) slice_products_kernel(
     const T *__restrict__ U, const T *__restrict__ S, const T *__restrict__ V,
     const int64_t *__restrict__ offsets, int64_t k, int64_t n1, int64_t n2, T *__restrict__ Out,
-    bool subtract, double *sumsq) {
+    bool subtract, double *sumsq, bool vtrans) {
   __shared__ __align__(16) T Us[TK][TM];
   __shared__ __align__(16) T Vs[TK][TN];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(NT) slice_products_kernel(
       int t = idx / TM, r = idx % TM;
       int64_t a = a0 + r, c = q0 + t;
       T v = T(0);
-      if (a < n1 && c < cnt) v = U[(c0 + c) * n1 + a] * S[c0 + c];
+      if (a < n1 && c < cnt) v = U[(c0 + c) * n1 + a] * (S ? S[c0 + c] : T(1));
       Us[t][r] = v;
     }
 #pragma unroll
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(NT) slice_products_kernel(
       int t = idx / TN, r = idx % TN;
       int64_t b = b0 + r, c = q0 + t;
       T v = T(0);
-      if (b < n2 && c < cnt) v = V[(c0 + c) * n2 + b];
+      if (b < n2 && c < cnt) v = vtrans ? V[c0 * n2 + b * k + c] : V[(c0 + c) * n2 + b];
       Vs[t][r] = v;
     }
     __syncthreads();
@@ -177,7 +177,21 @@ cudaError_t slice_products(const T *U, const T *S, const T *V, const int64_t *of
                            bool subtract_from_out, double *sumsq, cudaStream_t st) {
   dim3 grid((unsigned)((n1 + TM - 1) / TM), (unsigned)((n2 + TN - 1) / TN), (unsigned)n3);
   slice_products_kernel<T><<<grid, NT, 0, st>>>(U, S, V, offsets, k, n1, n2, Out,
-                                                subtract_from_out, sumsq);
+                                                subtract_from_out, sumsq, false);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t slice_rotate(const T *A, const T *V, int64_t rows, int64_t cols, int64_t n3, T *Out,
+                         bool tensor_cores, int *status, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (tensor_cores)
+      return slice_products_tc(A, nullptr, V, nullptr, cols, rows, cols, n3, Out, false,
+                               nullptr, status, st, true);
+  }
+  dim3 grid((unsigned)((rows + TM - 1) / TM), (unsigned)((cols + TN - 1) / TN), (unsigned)n3);
+  slice_products_kernel<T><<<grid, NT, 0, st>>>(A, nullptr, V, nullptr, cols, rows, cols, Out,
+                                                false, nullptr, true);
   return cudaGetLastError();
 }
 
@@ -207,6 +221,8 @@ cudaError_t backward_scalars(double *scal, double dL, cudaStream_t st) {
   template cudaError_t slice_products<T>(const T *, const T *, const T *, const int64_t *,  \
                                          int64_t, int64_t, int64_t, int64_t, T *, bool,     \
                                          double *, cudaStream_t);                           \
+  template cudaError_t slice_rotate<T>(const T *, const T *, int64_t, int64_t, int64_t, T *, \
+                                       bool, int *, cudaStream_t);                          \
   template cudaError_t gemm_atb<T>(const T *, const T *, int64_t, int64_t, T *,             \
                                    const double *, double *, size_t, cudaStream_t);
 INST(float)

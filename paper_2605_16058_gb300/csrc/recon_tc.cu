@@ -1,4 +1,5 @@
-// Slice products on the tensor cores: Out_i = U_i diag(S_i) V_i^T (or Out_i -= ...), the
+// Slice products on the tensor cores: Out_i = U_i diag(S_i) V_i^T (or Out_i -= ...; S may
+// be null for S = 1, and V may be read transposed, which gives the rotation A_i V_i), the
 // facewise product of the star-M product (Sec. 2.1, second step) for the factors of
 // t-SVDM-I (uniform k) or t-SVDM-II (packed, slice i's columns offsets[i]..offsets[i+1]-1),
 // FP32 data.  It is a dense contraction over the rank, so it runs on tcgen05:
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(RT, 1)
                              const float *__restrict__ V, const int64_t *__restrict__ offsets,
                              int64_t k, int64_t n1, int64_t n2, int64_t n3,
                              float *__restrict__ Out, bool subtract, double *sumsq,
-                             int *status) {
+                             int *status, bool vtrans) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ReconSmem &s = *reinterpret_cast<ReconSmem *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int PA[6] = {0, 0, 1, 0, 2, 1}, PB[6] = {0, 1, 0, 2, 0, 1};
@@ -84,7 +85,9 @@ __global__ void __launch_bounds__(RT, 1)
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               const int64_t c = (int64_t)kb * RK + ch * 8 + e + u;
-              x[u] = (a < n1 && c < cnt) ? __ldg(U + (c0 + c) * n1 + a) * __ldg(S + c0 + c) : 0.f;
+              x[u] = (a < n1 && c < cnt)
+                         ? __ldg(U + (c0 + c) * n1 + a) * (S ? __ldg(S + c0 + c) : 1.f)
+                         : 0.f;
             }
             __nv_bfloat16 p0, p1, p2, q0, q1, q2;
             tc::split3(x[0], p0, p1, p2);
@@ -114,7 +117,10 @@ __global__ void __launch_bounds__(RT, 1)
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               const int64_t c = (int64_t)kb * RK + ch * 8 + e + u;
-              x[u] = (bb < n2 && c < cnt) ? __ldg(V + (c0 + c) * n2 + bb) : 0.f;
+              // V(b, c) at (c0 + c) n2 + b, or (vtrans, uniform k) at c0 n2 + b k + c
+              x[u] = (bb < n2 && c < cnt)
+                         ? __ldg(vtrans ? V + c0 * n2 + bb * k + c : V + (c0 + c) * n2 + bb)
+                         : 0.f;
             }
             __nv_bfloat16 p0, p1, p2, q0, q1, q2;
             tc::split3(x[0], p0, p1, p2);
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(RT, 1)
 cudaError_t slice_products_tc(const float *U, const float *S, const float *V,
                               const int64_t *offsets, int64_t k, int64_t n1, int64_t n2,
                               int64_t n3, float *Out, bool subtract_from_out, double *sumsq,
-                              int *status, cudaStream_t st) {
+                              int *status, cudaStream_t st, bool vtrans) {
   const size_t smem = sizeof(ReconSmem) + 1024;
   cudaError_t e = cudaFuncSetAttribute(slice_products_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -210,7 +216,7 @@ cudaError_t slice_products_tc(const float *U, const float *S, const float *V,
   if (ntiles == 0) return cudaSuccess;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
   slice_products_tc_kernel<<<grid, RT, smem, st>>>(U, S, V, offsets, k, n1, n2, n3, Out,
-                                                  subtract_from_out, sumsq, status);
+                                                  subtract_from_out, sumsq, status, vtrans);
   return cudaGetLastError();
 }
 

@@ -5,7 +5,8 @@ L = sqrt(sum of discarded sigma^2) / ||X||_F at rank k.
 
 One training step, every part of it a libtsvdm kernel (torch only allocates):
   tsvdm_cayley          M = Cayley(A) M0 (Gauss-Jordan of I + W, two small GEMMs)
-  tsvdm_fixed_rank      forward: Ahat = X x_3 M, batched Jacobi SVDs, rank-k factors
+  tsvdm_fixed_rank      forward: Ahat = X x_3 M, batched Jacobi SVDs (optionally warm-started
+                        from the previous step's right vectors), rank-k factors
   tsvdm_backward        residual R = Ahat - U_k S_k V_k^T, L, dL/dM (and dL/dX if asked)
   tsvdm_cayley_backward dL/dA from dL/dM
   tsvdm_adam            A <- Adam(A, dL/dA)
@@ -26,7 +27,9 @@ class CayleyTrainer:
     """Holds the plan and every buffer of the training loop (allocated once)."""
 
     def __init__(self, X: torch.Tensor, M0: torch.Tensor, shape, k, lr=1e-3, betas=(0.9, 0.999),
-                 eps=1e-8, want_dX=False):
+                 eps=1e-8, want_dX=False, warm_start=False):
+        """warm_start: every step's slice SVDs start from the previous step's right vectors
+        (M moves by one Adam step at a time, so a few Jacobi sweeps suffice)."""
         n1, n2, n3 = shape
         self.shape, self.k, self.lr, self.betas, self.eps = shape, int(k), lr, betas, eps
         self.X = X
@@ -34,6 +37,8 @@ class CayleyTrainer:
         self.dtype = X.dtype
         dev = X.device
         self.plan = Plan(n1, n2, n3, dtype=self.dtype, orthogonal=True)
+        if warm_start:
+            self.plan.set_warm_start(True)
         self.A = torch.zeros(n3, n3, dtype=self.dtype, device=dev)
         self.m1 = torch.zeros_like(self.A)
         self.m2 = torch.zeros_like(self.A)

@@ -32,6 +32,7 @@ SIGNATURES = {
     "tsvdm_plan_set_jacobi": (_i32, [_vp, _dbl, _i32]),
     "tsvdm_plan_set_tuning": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
     "tsvdm_plan_set_engine": (_i32, [_vp, _i32]),
+    "tsvdm_plan_set_warm_start": (_i32, [_vp, _i32]),
     "tsvdm_transform": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "tsvdm_fixed_rank": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pdbl]),
     "tsvdm_tolerance": (_i32, [_vp, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _vp, _i64, _pi64, _pdbl]),
@@ -141,6 +142,11 @@ def tsvdm_plan_set_tuning(plan, block_width=0, cluster_size=0, clusters=0, stage
 def tsvdm_plan_set_engine(plan, engine):
     e = ENGINES[engine] if isinstance(engine, str) else int(engine)
     return check(lib().tsvdm_plan_set_engine(plan, e), "tsvdm_plan_set_engine")
+
+
+def tsvdm_plan_set_warm_start(plan, enable):
+    return check(lib().tsvdm_plan_set_warm_start(plan, int(bool(enable))),
+                 "tsvdm_plan_set_warm_start")
 
 
 def tsvdm_transform(plan, X, M, inverse, Y):

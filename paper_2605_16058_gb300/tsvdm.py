@@ -88,6 +88,10 @@ class Plan:
     def set_jacobi(self, tol=0.0, max_sweeps=0):
         N.tsvdm_plan_set_jacobi(self.handle, tol, max_sweeps)
 
+    def set_warm_start(self, enable=True):
+        """Start each decomposition's slice SVDs from the previous call's right vectors."""
+        N.tsvdm_plan_set_warm_start(self.handle, enable)
+
     def set_engine(self, engine):
         """Engine of the Jacobi Gram / rotation products: "auto", "fma" or "tc"."""
         N.tsvdm_plan_set_engine(self.handle, engine)

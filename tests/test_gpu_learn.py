@@ -132,3 +132,54 @@ def test_learned_transform_lowers_the_loss_and_matches_oracle_first_step():
     g1 = oracle.loss_and_grad(X, M1, k)
     assert abs(losses[1] - g1["loss"]) <= 1e-8 * g1["loss"]
     assert losses[-1] < losses[0]
+
+
+@pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-10), (torch.float32, 1e-4)])
+def test_warm_start_matches_cold_start(dt, tol):
+    """A sequence of slightly different transforms (the situation of learned-M training):
+    the warm-started decomposition equals the cold one (sigma, rank-k subspaces, relative
+    error) and needs fewer Jacobi sweeps."""
+    from paper_2605_16058_gb300.tsvdm import Plan
+    X = synth.crystal(shape=(96, 70, 12), lattice=(4, 3), dtype=np.float64)
+    n1, n2, n3 = X.shape
+    k = 4
+    rng = np.random.default_rng(31)
+    M0 = synth.dct2_matrix(n3)
+    warm, cold = Plan(n1, n2, n3, dtype=dt), Plan(n1, n2, n3, dtype=dt)
+    warm.set_warm_start(True)
+    Xd = t_lib(X, dtype=dt)
+    sw_w, sw_c = [], []
+    for it in range(4):
+        A = 1e-3 * it * rng.standard_normal((n3, n3))
+        M = oracle.cayley(A, M0)[0]
+        Md = t_lib(M, dtype=dt)
+        fw, fc = warm.fixed_rank(Xd, Md, k), cold.fixed_rank(Xd, Md, k)
+        sw_w.append(warm.stats()[0])
+        sw_c.append(cold.stats()[0])
+        Sw, Sc = np_lib(fw["S"]), np_lib(fc["S"])
+        assert np.max(np.abs(Sw - Sc)) <= tol * Sc.max()
+        assert abs(fw["rel_err"] - fc["rel_err"]) <= tol
+        Uw, Uc = np_lib(fw["U"]), np_lib(fc["U"])
+        for i in range(n3):
+            s_all = np.sort(np.linalg.svd(
+                np.einsum("it,abt->abi", M, X)[:, :, i], compute_uv=False))[::-1]
+            if s_all[k - 1] - s_all[k] > 1e-3 * s_all[0]:
+                P = lambda u: u @ u.T
+                assert np.linalg.norm(P(Uw[:, :, i]) - P(Uc[:, :, i])) <= 100 * tol
+    assert sum(sw_w[1:]) < sum(sw_c[1:])          # warm starts converge in fewer sweeps
+    # a new call of set_warm_start makes the next decomposition cold again
+    warm.set_warm_start(True)
+    warm.fixed_rank(Xd, Md, k)
+    assert warm.stats()[0] == cold.stats()[0]
+
+
+def test_learned_transform_with_warm_start_tracks_cold_training():
+    from paper_2605_16058_gb300.learn import CayleyTrainer
+    X = synth.crystal(shape=(64, 48, 16), lattice=(4, 3), dtype=np.float64)
+    M0 = synth.dct2_matrix(16)
+    args = (t_lib(X, dtype=torch.float64), t_lib(M0, dtype=torch.float64), X.shape, 3)
+    cold = CayleyTrainer(*args, lr=1e-3)
+    warm = CayleyTrainer(*args, lr=1e-3, warm_start=True)
+    lc, _ = cold.train(10)
+    lw, _ = warm.train(10)
+    assert max(abs(a - b) / a for a, b in zip(lc, lw)) <= 1e-9
