@@ -147,6 +147,17 @@ tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster
  * products U_i diag(S_i) V_i^T of F32 plans: tensor cores (AUTO, TC; three-term BF16
  * split, FP32-level accuracy) or FMA.
  * ENOTSUP for TC on an F64 plan, EINVAL for other values. */
+/* Data-driven transform (Sec. 2.2: M as the transposed matrix of left singular vectors of
+ * the mode-3 unfolding A_(3), an n3 x (n1 n2) matrix; an upfront SVD of the unfolding).
+ * Writes the orthogonal n3 x n3 M (column-major; device or host pointer) for the tensor X
+ * (n1 x n2 x n3, device or host) of a 3-way plan.  The left singular vectors of A_(3) are
+ * the eigenvectors of G = A_(3) A_(3)^T = X_mat^T X_mat (formed with FP64 partial sums in
+ * a fixed order); they come from the library's own Jacobi SVD of G (a one-slice plan kept
+ * inside this plan, allocated on the first call), by decreasing singular value, each with
+ * its largest-magnitude entry positive (rows of M with equal singular values are defined
+ * only up to a rotation).  Synchronises the plan's stream.  ENOTSUP on a d-way plan. */
+tsvdm_status tsvdm_data_transform(tsvdm_plan plan, const void *X, void *M);
+
 /* Warm start of the slice SVDs, for sequences of closely related tensors (learned-M
  * training, where M changes by one optimiser step at a time; streaming data).  Once
  * enabled, every decomposition after the first starts each slice's one-sided Jacobi from

@@ -147,6 +147,22 @@ def svd_slices(Ahat, max_sweeps=MAX_SWEEPS, threads=None):
     return U, S, V, sweeps
 
 
+def data_transform(X):
+    """Sec. 2.2's data-driven M: the transposed matrix of left singular vectors of the mode-3
+    unfolding A_(3) (n3 x n1 n2; row t is frontal slice t), by decreasing singular value,
+    each vector with its largest-magnitude entry positive.  The SVD is LAPACK's (a library
+    routine as one step).  Returns (M, sigma)."""
+    X = _f64(X)
+    n3 = X.shape[2]
+    A3 = X.reshape(-1, n3, order="F").T
+    W, sig, _ = np.linalg.svd(A3, full_matrices=True)
+    for j in range(W.shape[1]):
+        i = int(np.argmax(np.abs(W[:, j])))
+        if W[i, j] < 0:
+            W[:, j] = -W[:, j]
+    return W.T.copy(), sig
+
+
 def ttm_mode(X, M, mode):
     """Y = X x_mode M for a d-way X (Sec. 2.1's mode-k product; mode is 0-based):
     Y(.., i, ..) = sum_t M[i,t] X(.., t, ..).  Each trailing index combination is one

@@ -48,6 +48,10 @@ struct tsvdm_plan_s {
   // warm start of the slice SVDs: the next decomposition starts from the V in Vw
   int warm = 0, warm_valid = 0;
   void *warm_buf = nullptr;  // A_i V_i (rows cols n3 elements)
+  // data-driven transform: a one-slice n3 x n3 plan for the SVD of the mode-3 Gram, and its
+  // buffers (Gram, 1 x 1 identity, U, S, V)
+  tsvdm_plan_s *dsub = nullptr;
+  void *dbuf = nullptr;
   int tol_valid = 0;
   int64_t tol_total = 0;
   void *stage[STG_COUNT] = {};
@@ -471,6 +475,8 @@ void free_plan(tsvdm_plan_s *p) {
                   p->norm2, p->sched, p->dtmp, p->warm_buf};
   for (void *b : bufs)
     if (b) cudaFree(b);
+  if (p->dsub) free_plan(p->dsub);
+  if (p->dbuf) cudaFree(p->dbuf);
   for (int i = 0; i < STG_COUNT; ++i)
     if (p->stage[i]) cudaFree(p->stage[i]);
   for (int i = 0; i < 2 * TSVDM_STAGE_COUNT; ++i)
@@ -479,6 +485,47 @@ void free_plan(tsvdm_plan_s *p) {
 }
 
 }  // namespace
+
+// Data-driven M (Sec. 2.2): the transposed left singular vectors of the mode-3 unfolding,
+// i.e. the eigenvectors of G = X_mat^T X_mat, from the library's own Jacobi SVD of G.
+template <typename T>
+tsvdm_status data_transform_impl(tsvdm_plan_s *p, const void *X, void *M) {
+  const int64_t P = p->n1 * p->n2, n = p->n3;
+  const size_t e = p->esz;
+  void *dX, *dM;
+  bool sX, sM;
+  tsvdm_status s;
+  if ((s = stage_in(p, STG_X, X, e * P * n, true, &dX, &sX)) != TSVDM_OK) return s;
+  if ((s = stage_in(p, STG_M, M, e * n * n, false, &dM, &sM)) != TSVDM_OK) return s;
+  if (!p->dsub) {
+    tsvdm_plan sub = nullptr;
+    s = tsvdm_plan_create(n, n, 1, p->dtype, p->dtype == TSVDM_F32 ? TSVDM_P_FP32 : TSVDM_P_FP64,
+                          1, p->st, &sub);
+    if (s != TSVDM_OK) return s;
+    sub->engine = p->engine;
+    if (cudaMalloc(&p->dbuf, e * (3 * n * n + n + 16)) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(sub);
+      return TSVDM_ENOMEM;
+    }
+    p->dsub = sub;
+  }
+  T *G = (T *)p->dbuf, *one = G + n * n, *U = one + 16, *S = U + n * n, *V = S + n;
+  const T unit = T(1);
+  CK(cudaMemcpyAsync(one, &unit, sizeof(T), cudaMemcpyHostToDevice, p->st));
+  stage_begin(p, TSVDM_STAGE_OTHER);
+  CK(gemm_atb<T>((const T *)dX, (const T *)dX, P, n, G, nullptr, p->splitk, p->splitk_elems,
+                 p->st));
+  stage_end(p, TSVDM_STAGE_OTHER, 2);
+  // G = W diag(sigma) W^T (symmetric PSD): the one-slice t-SVD with M = [1] gives W in U
+  if ((s = fixed_rank_impl<T>(p->dsub, G, one, n, U, S, V, 0, nullptr)) != TSVDM_OK) return s;
+  stage_begin(p, TSVDM_STAGE_OTHER);
+  CK(transpose_slices<T>(U, n, n, 1, (T *)dM, p->st));         // M = W^T
+  stage_end(p, TSVDM_STAGE_OTHER, 1);
+  if (sM) CK(cudaMemcpyAsync(M, dM, e * n * n, cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return TSVDM_OK;
+}
 
 extern "C" {
 
@@ -646,6 +693,14 @@ tsvdm_status tsvdm_plan_set_engine(tsvdm_plan plan, int engine) {
   plan->engine = engine == TSVDM_JACOBI_TC ? JACOBI_TC
                                            : (engine == TSVDM_JACOBI_FMA ? JACOBI_FMA : JACOBI_AUTO);
   return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_data_transform(tsvdm_plan plan, const void *X, void *M) {
+  if (!valid_plan(plan) || !X || !M) return TSVDM_EINVAL;
+  if (plan->dw) return TSVDM_ENOTSUP;
+  begin_call(plan);
+  if (plan->dtype == TSVDM_F32) return data_transform_impl<float>(plan, X, M);
+  return data_transform_impl<double>(plan, X, M);
 }
 
 tsvdm_status tsvdm_plan_set_warm_start(tsvdm_plan plan, int enable) {

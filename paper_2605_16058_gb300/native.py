@@ -33,6 +33,7 @@ SIGNATURES = {
     "tsvdm_plan_set_tuning": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
     "tsvdm_plan_set_engine": (_i32, [_vp, _i32]),
     "tsvdm_plan_set_warm_start": (_i32, [_vp, _i32]),
+    "tsvdm_data_transform": (_i32, [_vp, _vp, _vp]),
     "tsvdm_transform": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "tsvdm_fixed_rank": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pdbl]),
     "tsvdm_tolerance": (_i32, [_vp, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _vp, _i64, _pi64, _pdbl]),
@@ -147,6 +148,10 @@ def tsvdm_plan_set_engine(plan, engine):
 def tsvdm_plan_set_warm_start(plan, enable):
     return check(lib().tsvdm_plan_set_warm_start(plan, int(bool(enable))),
                  "tsvdm_plan_set_warm_start")
+
+
+def tsvdm_data_transform(plan, X, M):
+    return check(lib().tsvdm_data_transform(plan, _ptr(X), _ptr(M)), "tsvdm_data_transform")
 
 
 def tsvdm_transform(plan, X, M, inverse, Y):

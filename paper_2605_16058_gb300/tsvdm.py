@@ -88,6 +88,13 @@ class Plan:
     def set_jacobi(self, tol=0.0, max_sweeps=0):
         N.tsvdm_plan_set_jacobi(self.handle, tol, max_sweeps)
 
+    def data_transform(self, X, out=None):
+        """The data-driven M (transposed left singular vectors of the mode-3 unfolding),
+        an n3 x n3 buffer in library layout."""
+        out = out if out is not None else self._empty(self.n3, self.n3)
+        N.tsvdm_data_transform(self.handle, X, out)
+        return out
+
     def set_warm_start(self, enable=True):
         """Start each decomposition's slice SVDs from the previous call's right vectors."""
         N.tsvdm_plan_set_warm_start(self.handle, enable)

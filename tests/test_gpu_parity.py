@@ -337,3 +337,54 @@ def test_argument_errors():
     with pytest.raises(native.TsvdmError) as e:
         plan.fixed_rank(X, M, 11)
     assert e.value.status == native.EINVAL
+
+
+# ---------------------------------------------------------------- data-driven M
+@pytest.mark.parametrize("dt,shape", [(torch.float64, (60, 40, 12)),
+                                      (torch.float32, (200, 130, 24))])
+def test_data_transform_matches_oracle(dt, shape):
+    """M from the library's Jacobi SVD of the mode-3 Gram against LAPACK's SVD of the
+    unfolding: orthogonal, diagonalising the mode-3 Gram, the same rows (sign rule) where
+    the singular values are well separated, and the same t-SVDM-I error."""
+    rng = np.random.default_rng(43)
+    n1, n2, n3 = shape
+    X = synth.cp_tensor(n1, n2, n3, 8, rng, noise_rel=0.2)
+    if dt == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+    Mo, sig = oracle.data_transform(X)
+    plan = _plan(n1, n2, n3, dt)
+    Xd = t_lib(X, dtype=dt)
+    Mg = np_lib(plan.data_transform(Xd))
+    tol = 1e-10 if dt == torch.float64 else 2e-5
+    assert np.max(np.abs(Mg @ Mg.T - np.eye(n3))) <= tol
+    A3 = X.reshape(-1, n3, order="F").T
+    G = A3 @ A3.T
+    D = Mg @ G @ Mg.T
+    assert np.max(np.abs(D - np.diag(np.diag(D)))) <= 10 * tol * np.max(np.abs(G))
+    s2 = sig ** 2
+    for j in range(n3):
+        gap = min(abs(s2[j] - s2[j - 1]) if j > 0 else np.inf,
+                  abs(s2[j] - s2[j + 1]) if j + 1 < n3 else np.inf)
+        if gap > 1e-2 * s2[0]:
+            assert np.max(np.abs(Mg[j] - Mo[j])) <= 100 * tol * s2[0] / gap, j
+    k = 5
+    out = plan.fixed_rank(Xd, t_lib(Mg, dtype=dt), k)
+    ref = oracle.fixed_rank(X, Mo, k)
+    assert abs(out["rel_err"] - ref["rel_err"]) <= (1e-5 if dt == torch.float32 else 1e-9)
+
+
+def test_data_transform_host_buffers_and_errors():
+    from paper_2605_16058_gb300 import native as N
+    rng = np.random.default_rng(44)
+    X = synth.cp_tensor(30, 20, 6, 4, rng, noise_rel=0.2)
+    plan = _plan(30, 20, 6, torch.float64)
+    dev = np_lib(plan.data_transform(t_lib(X, dtype=torch.float64)))
+    host = torch.empty(6, 6, dtype=torch.float64)
+    N.tsvdm_data_transform(plan.handle, t_lib(X, dtype=torch.float64).cpu(), host)
+    assert np.array_equal(np_lib(host), dev)
+    from paper_2605_16058_gb300.tsvdm import Plan
+    p4 = Plan.dway((10, 8, 3, 2), dtype=torch.float64)
+    with pytest.raises(N.TsvdmError) as e:
+        p4.data_transform(torch.zeros(2, 3, 8, 10, dtype=torch.float64, device="cuda"),
+                          out=torch.empty(6, 6, dtype=torch.float64, device="cuda"))
+    assert e.value.status == N.ENOTSUP

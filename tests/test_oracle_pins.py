@@ -463,3 +463,25 @@ def test_dway_original_domain_factors_rebuild_x():
     back = oracle.to_slices(oracle.dway_transform(U.reshape((7, 6, 2, 3), order="F"), Ms))
     assert np.max(np.abs(back - f["U"])) <= 1e-13
     assert oracle.rel_err_direct(X, Xk) <= 1e-12
+
+
+# ---------------------------------------------------------------- data-driven M
+def test_data_transform_diagonalises_the_mode3_gram():
+    """M's rows are the left singular vectors of A_(3): M is orthogonal and
+    M A_(3) A_(3)^T M^T = diag(sigma^2), decreasing (with M^T in place of M the product is
+    not diagonal, so a transposition fails here); the transformed slices carry the
+    energies sigma_i^2."""
+    rng = np.random.default_rng(41)
+    X = synth.cp_tensor(20, 15, 9, 6, rng, noise_rel=0.3)
+    M, sig = oracle.data_transform(X)
+    assert np.max(np.abs(M @ M.T - np.eye(9))) <= 1e-12
+    A3 = X.reshape(-1, 9, order="F").T
+    D = M @ (A3 @ A3.T) @ M.T
+    assert np.max(np.abs(D - np.diag(np.diag(D)))) <= 1e-10 * np.max(np.abs(D))
+    assert np.allclose(np.diag(D), sig ** 2, rtol=1e-10)
+    assert np.all(np.diff(np.diag(D)) <= 0)
+    Ahat = oracle.ttm3(X, M)
+    energies = np.array([np.sum(Ahat[:, :, i] ** 2) for i in range(9)])
+    assert np.allclose(energies, sig ** 2, rtol=1e-10)
+    for j in range(9):                              # sign rule
+        assert M[j, np.argmax(np.abs(M[j]))] > 0
