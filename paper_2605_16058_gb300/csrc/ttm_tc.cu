@@ -11,13 +11,14 @@
 //   TF32    D += A B with both operands rounded to TF32 (one kind::tf32 MMA per k-step)
 //
 // Persistent: one CTA per SM (a kernel that holds tensor memory runs one CTA per SM)
-// loops over row tiles; the stage ring runs across tiles.  Warp roles (384 threads):
+// loops over row tiles; the stage ring runs across tiles.  Warp roles (512 threads):
 //   warp 0       TMA producer: raw FP32 X tile (128 rows x 32 t, no swizzle) and the
 //                pre-converted K-major B tiles (swizzled) of each stage;
 //   warp 1       TMEM allocation; one thread issues the MMAs and commits them (a tile's
 //                first MMA waits until the epilogue has read the previous accumulator);
-//   warps 4..7   converters (thread = row): FP32 X -> K-major swizzled operand tiles;
-//   warps 8..11  epilogue (tcgen05.ld of its own TMEM lane -> scale -> store), which
+//   warps 4..11  converters (two threads per row, 16 t each): FP32 X -> K-major swizzled
+//                operand tiles;
+//   warps 12..15 epilogue (tcgen05.ld of its own TMEM lane -> scale -> store), which
 //                overlaps the next tile's loads and conversions.
 // Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT in the status
 // word, every role leaves its loop and TMEM is released.  Nothing traps.
@@ -34,7 +35,7 @@ namespace {
 constexpr int TBM = 128;
 constexpr int TBK = 32;
 constexpr int MAX_STAGES = 4;
-constexpr int TC_THREADS = 384;   // warps 0 TMA, 1 MMA + TMEM, 4-7 converters, 8-11 epilogue
+constexpr int TC_THREADS = 512;   // warps 0 TMA, 1 MMA + TMEM, 4-11 converters, 12-15 epilogue
 constexpr unsigned SPIN_LIMIT = 1u << 26;
 
 struct TcParams {
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     s_fail = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 128);
+      mbar_init(&conv[s], 256);
       mbar_init(&empty[s], 1);
     }
     mbar_init(tfull, 1);
@@ -224,9 +225,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       if (ok) mma_commit(tfull);
     }
-  } else if (warp >= 4 && warp < 8) {
-    // ---------------- converters (thread = row): FP32 X -> K-major swizzled operands
-    const int row = tid - 128;
+  } else if (warp >= 4 && warp < 12) {
+    // ---------------- converters (two threads per row, 16 t each): FP32 X -> K-major
+    // swizzled operands
+    const int row = (tid - 128) & 127, kh = (tid - 128) >> 7;
     double ss = 0.0;
     const bool do_ss = p.sumsq != nullptr;
     int it = 0;
@@ -237,21 +239,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!wait(&full[s], u & 1)) { ok = false; break; }
         unsigned char *st = smem + s * L.stage;
         const float *raw = (const float *)(st + L.raw);
-        float x[TBK];
+        constexpr int KH = TBK / 2;
+        float x[KH];
 #pragma unroll
-        for (int k = 0; k < TBK; ++k) x[k] = raw[k * TBM + row];
+        for (int k = 0; k < KH; ++k) x[k] = raw[(kh * KH + k) * TBM + row];
         if (do_ss) {
 #pragma unroll
-          for (int k = 0; k < TBK; ++k) ss += (double)x[k] * (double)x[k];
+          for (int k = 0; k < KH; ++k) ss += (double)x[k] * (double)x[k];
         }
         if (bf) {
           unsigned char *ahi = st + L.a, *alo = st + L.a + TBM * 64;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c = kh * 2 + cc;
             uint32_t h[4], l[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              float x0 = x[c * 8 + 2 * q], x1 = x[c * 8 + 2 * q + 1];
+              float x0 = x[cc * 8 + 2 * q], x1 = x[cc * 8 + 2 * q + 1];
               __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
               __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
               __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
@@ -265,11 +269,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         } else {
           unsigned char *a = st + L.a;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
+          for (int cc = 0; cc < 4; ++cc) {
+            const int c = kh * 4 + cc;
             uint32_t v[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v[q]) : "f"(x[c * 4 + q]));
+              asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v[q]) : "f"(x[cc * 4 + q]));
             const uint32_t off = (uint32_t)row * 128 + (((uint32_t)c ^ ((uint32_t)row & 7)) << 4);
             *(uint4 *)(a + off) = make_uint4(v[0], v[1], v[2], v[3]);
           }
@@ -283,10 +288,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       if (lane == 0) atomicAdd(p.sumsq, ss);
     }
-  } else if (warp >= 8) {
+  } else if (warp >= 12) {
     // ---------------- epilogue (thread = TMEM lane = row): scale, optional beta Z, store
-    const int row = tid - 256;
-    const uint32_t lane_base = (uint32_t)(32 * (warp - 8)) << 16;
+    const int row = tid - 384;
+    const uint32_t lane_base = (uint32_t)(32 * (warp - 12)) << 16;
     const float scale = p.scale_ptr ? (float)(*p.scale_ptr) : 1.f;
     const float beta = p.beta_ptr ? (float)(*p.beta_ptr) : 0.f;
     int j = 0;
