@@ -105,6 +105,7 @@ constexpr int MAXSORT = 1024;        // slices with more columns keep the natura
 
 template <typename T, int W2, int NS>
 struct Smem {
+  static constexpr bool QCOL = false;    // Q row-major
   T buf[Cfg<T, W2, NS>::BUF];            // streamed chunk / Gram partials
   T G[2][W2 * (W2 + 1) / 2];         // Gram, packed upper triangle, double-buffered
   __align__(16) T Q[W2 * W2];        // accumulated rotation, Q(r, j) at Q[r*W2 + j]
@@ -152,13 +153,14 @@ struct GroupBar {
 // member names match Smem, so the inner Gram sweep is shared.  3 CTAs fit on an SM.
 struct SmemTc {
   static constexpr int W2 = 64;
+  static constexpr bool QCOL = true;       // Q column-major
   // operand tiles (Gram: two 16 KB [128 x 32] TF32 tiles; apply: the hi and lo
   // [128 x 32] tiles of one K-block), then the Gram epilogue scratch and the sort keys
   __align__(1024) unsigned char op[32768];
   union {
     struct {
       float G[2][W2 * (W2 + 1) / 2];       // Gram, packed upper triangle, double-buffered
-      __align__(16) float Q[W2 * W2];      // accumulated rotation, Q(r, j) at Q[r*W2 + j]
+      __align__(16) float Q[W2 * W2];      // accumulated rotation, column-major: Q(r, j) at Q[j*W2 + r]
     };
     // the apply's B operand, (Q - I) split into TF32 hi (first 16 KB) and lo, each two
     // K-blocks of [64 output columns x 32 K] (G and Q are dead while it lives)
@@ -522,17 +524,35 @@ __device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, c
         Gd[tri<W2>(j1, i2)] = o10;
         Gd[tri<W2>(j1, j2)] = o11;
       }
-      // Q <- Q J: lane -> pair k = lane mod NP and a row offset; a warp covers 32 / NP rows
-      // at a time (distinct columns of a row across the pairs)
-      constexpr int RPW = 32 / NP;
-      const int k = lane % NP;
-      if (s.rot[sl][k]) {
-        const int i = s.pi[sl][k], j = s.pj[sl][k];
-        const T c = s.cs[sl][2 * k], sn = s.cs[sl][2 * k + 1];
-        for (int r = warp * RPW + lane / NP; r < W2; r += (NU / 32) * RPW) {
-          const T x = s.Q[r * W2 + i], y = s.Q[r * W2 + j];
-          s.Q[r * W2 + i] = c * x - sn * y;
-          s.Q[r * W2 + j] = sn * x + c * y;
+      if constexpr (SM::QCOL) {
+        // Q <- Q J on a column-major Q: item (pair k, rows 4 r4 .. 4 r4 + 3), one 16-byte
+        // load and store per column; a warp's items cover two pairs' full columns
+        constexpr int R4 = W2 / 4;
+        for (int it = tid; it < NP * R4; it += NU) {
+          const int k = it / R4, r4 = it % R4;
+          if (!s.rot[sl][k]) continue;
+          const T c = s.cs[sl][2 * k], sn = s.cs[sl][2 * k + 1];
+          float4 *qi = reinterpret_cast<float4 *>(&s.Q[s.pi[sl][k] * W2]) + r4;
+          float4 *qj = reinterpret_cast<float4 *>(&s.Q[s.pj[sl][k] * W2]) + r4;
+          const float4 x = *qi, y = *qj;
+          *qi = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z,
+                            c * x.w - sn * y.w);
+          *qj = make_float4(sn * x.x + c * y.x, sn * x.y + c * y.y, sn * x.z + c * y.z,
+                            sn * x.w + c * y.w);
+        }
+      } else {
+        // Q <- Q J: lane -> pair k = lane mod NP and a row offset; a warp covers 32 / NP
+        // rows at a time (distinct columns of a row across the pairs)
+        constexpr int RPW = 32 / NP;
+        const int k = lane % NP;
+        if (s.rot[sl][k]) {
+          const int i = s.pi[sl][k], j = s.pj[sl][k];
+          const T c = s.cs[sl][2 * k], sn = s.cs[sl][2 * k + 1];
+          for (int r = warp * RPW + lane / NP; r < W2; r += (NU / 32) * RPW) {
+            const T x = s.Q[r * W2 + i], y = s.Q[r * W2 + j];
+            s.Q[r * W2 + i] = c * x - sn * y;
+            s.Q[r * W2 + j] = sn * x + c * y;
+          }
         }
       }
     }
@@ -777,13 +797,13 @@ __device__ void build_bq(SmemTc &s, int tid, const GroupBar &bar) {
   float qv[W2 * W2 / NT];
 #pragma unroll
   for (int m = 0; m < W2 * W2 / NT; ++m) {
-    const int idx = tid + NT * m, c = idx >> 6, cp = idx & 63;
-    qv[m] = s.Q[c * W2 + cp] - (c == cp ? 1.f : 0.f);
+    const int idx = tid + NT * m, cp = idx >> 6, c = idx & 63;
+    qv[m] = s.Q[cp * W2 + c] - (c == cp ? 1.f : 0.f);
   }
   bar.sync();
 #pragma unroll
   for (int m = 0; m < W2 * W2 / NT; ++m) {
-    const int idx = tid + NT * m, c = idx >> 6, cp = idx & 63;
+    const int idx = tid + NT * m, cp = idx >> 6, c = idx & 63;
     __nv_bfloat16 t[3];
     split3(qv[m], t[0], t[1], t[2]);
     const uint32_t kb = (uint32_t)c >> 5, k = (uint32_t)c & 31;
