@@ -102,6 +102,7 @@ __device__ __forceinline__ void rot_block(T b00, T b01, T b10, T b11, T c1, T s1
 }
 
 constexpr int MAXSORT = 1024;        // slices with more columns keep the natural order
+constexpr int XLD = 33;              // row stride of the cross-sweep Gram quadrants
 
 template <typename T, int W2, int NS>
 struct Smem {
@@ -159,7 +160,14 @@ struct SmemTc {
   __align__(1024) unsigned char op[32768];
   union {
     struct {
-      float G[2][W2 * (W2 + 1) / 2];       // Gram, packed upper triangle, double-buffered
+      union {
+        // full inner sweeps (the first round of a sweep): Gram, packed upper triangle,
+        // double-buffered
+        float G[2][W2 * (W2 + 1) / 2];
+        // cross inner sweeps: the Gram's quadrants I x I, I x J and J x J (I = local
+        // columns 0..31, J = 32..63), row stride XLD, updated in place
+        float X3[3][32 * XLD];
+      };
       __align__(16) float Q[W2 * W2];      // accumulated rotation, column-major: Q(r, j) at Q[j*W2 + r]
     };
     // the apply's B operand, (Q - I) split into TF32 hi (first 16 KB) and lo, each two
@@ -675,7 +683,7 @@ __device__ __forceinline__ void put_chunk(unsigned char *tile, uint32_t row, uin
 // epilogue), so it needs no barrier to read them back; unaligned columns load directly.
 constexpr int GRING = 4;
 __device__ void gram_tc(SmemTc &s, const float *__restrict__ Wsl, int rows, int lda,
-                        uint32_t &phase, int tid, const GroupBar &bar) {
+                        uint32_t &phase, int tid, const GroupBar &bar, bool cross) {
   constexpr int W2 = SmemTc::W2;
   constexpr int GK = 32;
   static_assert(GRING * W2 * GK * sizeof(float) <= sizeof(SmemTc::bq), "Gram ring");
@@ -760,7 +768,40 @@ __device__ void gram_tc(SmemTc &s, const float *__restrict__ Wsl, int rows, int 
   }
   tc::fence_before_sync();
   bar.sync();
-  if (warp < 2) {
+  if (cross) {
+    // quadrants for the cross sweeps: warp 0 writes rows 0..31 of I x I and I x J, warp 1
+    // rows 32..63 of J x J (both triangles of the diagonal quadrants)
+    if (warp == 0) {
+      float *A = s.X3[0], *B = s.X3[1];
+#pragma unroll
+      for (int j0 = 0; j0 < W2; j0 += 16) {
+        float d[16];
+        tc::tmem_ld16(s.tmem + j0, d);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int j = j0 + e;
+          const float g = (d[e] + S[lane * 64 + (j ^ lane)]) + S[j * 64 + (lane ^ j)];
+          if (j < 32)
+            A[lane * XLD + j] = g;
+          else
+            B[lane * XLD + (j - 32)] = g;
+        }
+      }
+    } else if (warp == 1) {
+      float *C = s.X3[2];
+      const int i = 32 + lane;
+#pragma unroll
+      for (int j0 = 32; j0 < W2; j0 += 16) {
+        float d[16];
+        tc::tmem_ld16(s.tmem + ((uint32_t)32 << 16) + j0, d);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int j = j0 + e;
+          C[lane * XLD + (j - 32)] = (d[e] + S[i * 64 + (j ^ i)]) + S[j * 64 + (i ^ j)];
+        }
+      }
+    }
+  } else if (warp < 2) {
     const int i = warp * 32 + lane;
 #pragma unroll
     for (int j0 = 0; j0 < W2; j0 += 16) {
@@ -896,6 +937,173 @@ __device__ void apply_tc(SmemTc &s, float *__restrict__ W, int rows, int lda, ui
     }
     tc::fence_before_sync();
     bar.sync();                                    // TMEM read before the next chunk's MMAs
+  }
+}
+
+// Rotation of pair k from its Gram entries a = g_ii, b = g_jj, g = g_ij (FP32 slices): the
+// test and angle of pair_angle, stored in slot `sl` (c, s; rotated diagonal; flag).
+__device__ __forceinline__ void cross_angle(SmemTc &s, int sl, int k, float a, float b, float g,
+                                            float tol, float tol2) {
+  int rot = 0;
+  float c = 1.f, sn = 0.f;
+  if (!(isfinite(a) && isfinite(b))) {
+    s.nonfinite = 1;
+  } else if (rot_test_f32(a, b, g, tol, tol2)) {
+    const float h = b - a, g2 = 2.f * g;
+    float t = fabsf(g2) / (fabsf(h) + hypotf(h, g2));
+    if ((h >= 0.f) != (g2 >= 0.f)) t = -t;
+    c = __frsqrt_rn(fmaf(t, t, 1.f));
+    sn = c * t;
+    s.dd[sl][2 * k] = fmaf(-t, g, a);
+    s.dd[sl][2 * k + 1] = fmaf(t, g, b);
+    rot = 1;
+    s.any_rot = 1;
+    s.step_rot = 1;
+    atomicAdd((unsigned long long *)&s.nrot, 1ull);
+  }
+  s.cs[sl][2 * k] = c;
+  s.cs[sl][2 * k + 1] = sn;
+  s.rot[sl][k] = rot;
+}
+
+// One cross inner sweep of the tensor-core worker: every pair of a local column i < 32 with
+// a local column 32 + j, in 32 steps (step t pairs column k with column 32 + (k + t) mod 32),
+// on the quadrant storage X3 (A = I x I, B = I x J, C = J x J), accumulating the rotations
+// in Q.  Sets s.any_rot and s.step_rot.
+//
+// Thread-owned 2 x 2 blocks, updated in place.  In step t, block (p, q) (p <= q) holds
+//   A(p, q), B(p, (q + t) mod 32), B(q, (p + t) mod 32), C((p + t) mod 32, (q + t) mod 32),
+// the rows and columns of pairs p and q; no two blocks share an entry, so a block is read
+// and rewritten by its owner alone, and blocks of two non-rotating pairs are skipped.  The
+// next step's pair k joins column k with the J column of pair k + 1, so its cross entry is
+// in block (k, k + 1) (block (0, 31) for k = 31).  Lane k of the last warp owns that block:
+// it rotates it and forms pair k's next rotation from the entry it has just computed, while
+// the other warps rotate the remaining blocks and Q.  One barrier per step.  With row
+// stride 33 the loads and stores of a warp's blocks fall on distinct banks.
+__device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
+                                  const GroupBar &bar) {
+  constexpr int W2 = SmemTc::W2;
+  constexpr int NP = W2 / 2;
+  constexpr int NB = NP * (NP + 1) / 2;
+  constexpr int AW = NT / 32 - 1;          // the angle warp
+  constexpr int NU = NT - 32;              // update threads
+  constexpr int BPT = (NB + NU - 1) / NU;
+  float *A = s.X3[0], *B = s.X3[1], *C = s.X3[2];
+  const float tolf = (float)tol, tol2f = (float)(tol * tol);
+  const int warp = tid >> 5, lane = tid & 31;
+  // fresh-Gram convergence test |g| > tol sqrt(a b) over the cross pairs
+  int need = 0;
+  for (int idx = tid; idx < NP * NP; idx += NT) {
+    const int i = idx >> 5, j = idx & 31;
+    if (rot_test_f32(A[i * XLD + i], C[j * XLD + j], B[i * XLD + j], tolf, tol2f)) need = 1;
+  }
+  bar.sync();                        // every thread has read step_rot of the previous call
+  if (tid == 0) {
+    s.step_rot = 0;
+    if (first) s.any_rot = 0;
+  }
+  if (!bar.sync_or(need)) return;
+  if (first) {
+    for (int idx = tid; idx < W2 * W2; idx += NT) s.Q[idx] = (idx / W2 == idx % W2) ? 1.f : 0.f;
+  }
+  // update threads: blocks of the packed upper triangle of the NP x NP block grid, except
+  // the angle warp's blocks (k, k + 1) and (0, NP - 1)
+  int bp[BPT], bq[BPT];
+#pragma unroll
+  for (int t = 0; t < BPT; ++t) {
+    const int blk = tid + t * NU;
+    bp[t] = -1;
+    bq[t] = 0;
+    if (warp != AW && blk < NB) {
+      int pp = 0, start = 0;
+      while (start + (NP - pp) <= blk) {
+        start += NP - pp;
+        ++pp;
+      }
+      const int qq = pp + (blk - start);
+      if (qq != pp + 1 && !(pp == 0 && qq == NP - 1)) {
+        bp[t] = pp;
+        bq[t] = qq;
+      }
+    }
+  }
+  // angle warp: lane k owns block (hp, hq) and forms pair k's rotations; the entry it
+  // needs is o01 of (k, k + 1) or o10 of (0, NP - 1)
+  const int hp = lane < NP - 1 ? lane : 0, hq = lane < NP - 1 ? lane + 1 : NP - 1;
+  const int kq = (lane + 1) & 31;
+  if (warp == AW)                    // rotations of step 0: pair k = columns k, 32 + k
+    cross_angle(s, 0, lane, A[lane * XLD + lane], C[lane * XLD + lane], B[lane * XLD + lane],
+                tolf, tol2f);
+  bar.sync();
+  for (int step = 0; step < NP; ++step) {
+    const int sl = step & 1;
+    if (warp == AW) {
+      const int rp = s.rot[sl][hp], rq = s.rot[sl][hq];
+      const int sp = (hp + step) & 31, sq = (hq + step) & 31;
+      const bool more = step + 1 < NP;
+      if (rp || rq || more) {
+        float o00, o01, o10, o11;
+        rot_block(A[hp * XLD + hq], B[hp * XLD + sq], B[hq * XLD + sp], C[sp * XLD + sq],
+                  s.cs[sl][2 * hp], s.cs[sl][2 * hp + 1], s.cs[sl][2 * hq],
+                  s.cs[sl][2 * hq + 1], o00, o01, o10, o11);
+        if (rp || rq) {
+          A[hp * XLD + hq] = o00;
+          B[hp * XLD + sq] = o01;
+          B[hq * XLD + sp] = o10;
+          C[sp * XLD + sq] = o11;
+          C[sq * XLD + sp] = o11;
+        }
+        if (more) {
+          // the diagonal entries are the rotated ones if those pairs rotated, else
+          // unchanged in place
+          const int skq = (kq + step) & 31;
+          const float a = s.rot[sl][lane] ? s.dd[sl][2 * lane] : A[lane * XLD + lane];
+          const float b = s.rot[sl][kq] ? s.dd[sl][2 * kq + 1] : C[skq * XLD + skq];
+          cross_angle(s, sl ^ 1, lane, a, b, lane < NP - 1 ? o01 : o10, tolf, tol2f);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < BPT; ++t) {
+        const int p = bp[t], q = bq[t];
+        if (p < 0) continue;
+        const int rp = s.rot[sl][p], rq = s.rot[sl][q];
+        const int sp = (p + step) & 31, sq = (q + step) & 31;
+        if (p == q) {
+          if (rp) {
+            A[p * XLD + p] = s.dd[sl][2 * p];
+            C[sp * XLD + sp] = s.dd[sl][2 * p + 1];
+            B[p * XLD + sp] = 0.f;
+          }
+          continue;
+        }
+        if (!(rp || rq)) continue;
+        float o00, o01, o10, o11;
+        rot_block(A[p * XLD + q], B[p * XLD + sq], B[q * XLD + sp], C[sp * XLD + sq],
+                  s.cs[sl][2 * p], s.cs[sl][2 * p + 1], s.cs[sl][2 * q], s.cs[sl][2 * q + 1],
+                  o00, o01, o10, o11);
+        A[p * XLD + q] = o00;
+        B[p * XLD + sq] = o01;
+        B[q * XLD + sp] = o10;
+        C[sp * XLD + sq] = o11;
+        C[sq * XLD + sp] = o11;
+      }
+      // Q <- Q J on the column-major Q: item (pair k, rows 4 r4 .. 4 r4 + 3)
+      constexpr int R4 = W2 / 4;
+      for (int it = tid; it < NP * R4; it += NU) {
+        const int k = it / R4, r4 = it % R4;
+        if (!s.rot[sl][k]) continue;
+        const float c = s.cs[sl][2 * k], sn = s.cs[sl][2 * k + 1];
+        float4 *qi = reinterpret_cast<float4 *>(&s.Q[k * W2]) + r4;
+        float4 *qj = reinterpret_cast<float4 *>(&s.Q[(NP + ((k + step) & 31)) * W2]) + r4;
+        const float4 x = *qi, y = *qj;
+        *qi = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z,
+                          c * x.w - sn * y.w);
+        *qj = make_float4(sn * x.x + c * y.x, sn * x.y + c * y.y, sn * x.z + c * y.z,
+                          sn * x.w + c * y.w);
+      }
+    }
+    bar.sync();
   }
 }
 
@@ -1270,14 +1478,23 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
     }
     pair_columns<W2>(s, bi, bj, v.cols, sorted, tid);
     gbar.sync();
-    gram_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
+    // the first round of a sweep also rotates within each block (full inner sweeps), the
+    // others only across the two blocks
+    const bool cross = round != 0;
+    gram_tc(s, v.W, v.rows, v.rows, phase, tid, gbar, cross);
     for (int is = 0; is < p.inner_sweeps; ++is) {
-      inner_sweep<float, W2, 2>(s, tol, round == 0, is == 0, tid, gbar);
+      if (cross)
+        inner_sweep_cross(s, tol, is == 0, tid, gbar);
+      else
+        inner_sweep<float, W2, 2>(s, tol, true, is == 0, tid, gbar);
       if (!s.step_rot) break;
     }
     gbar.sync();
-    if (sorted && tid < W2 && s.col[tid] >= 0)     // squared norms after this step
-      __stcg(v.nrm2 + s.col[tid], s.G[s.gcur][tri<W2>(tid, tid)]);
+    if (sorted && tid < W2 && s.col[tid] >= 0) {   // squared norms after this step
+      const int c = tid & 31;
+      __stcg(v.nrm2 + s.col[tid], !cross ? s.G[s.gcur][tri<W2>(tid, tid)]
+                                         : s.X3[tid < 32 ? 0 : 2][c * XLD + c]);
+    }
     if (s.any_rot) {
       build_bq(s, tid, gbar);
       apply_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
