@@ -1063,11 +1063,16 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
         }
       }
     } else {
+      // (c, s) of the step's pairs; a pair with s == 0 is the identity (a non-rotating pair
+      // carries (1, 0); a rotation whose tangent underflowed has c = 1, s = 0 and leaves its
+      // diagonal unchanged), so s != 0 decides whether a pair moves
+      const float2 *cs2 = reinterpret_cast<const float2 *>(s.cs[sl]);
 #pragma unroll
       for (int t = 0; t < BPT; ++t) {
         const int p = bp[t], q = bq[t];
         if (p < 0) continue;
-        const int rp = s.rot[sl][p], rq = s.rot[sl][q];
+        const float2 cp = cs2[p], cq = cs2[q];
+        const bool rp = cp.y != 0.f, rq = cq.y != 0.f;
         const int sp = (p + step) & 31, sq = (q + step) & 31;
         if (p == q) {
           if (rp) {
@@ -1079,21 +1084,23 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
         }
         if (!(rp || rq)) continue;
         float o00, o01, o10, o11;
-        rot_block(A[p * XLD + q], B[p * XLD + sq], B[q * XLD + sp], C[sp * XLD + sq],
-                  s.cs[sl][2 * p], s.cs[sl][2 * p + 1], s.cs[sl][2 * q], s.cs[sl][2 * q + 1],
-                  o00, o01, o10, o11);
+        rot_block(A[p * XLD + q], B[p * XLD + sq], B[q * XLD + sp], C[sp * XLD + sq], cp.x,
+                  cp.y, cq.x, cq.y, o00, o01, o10, o11);
         A[p * XLD + q] = o00;
         B[p * XLD + sq] = o01;
         B[q * XLD + sp] = o10;
         C[sp * XLD + sq] = o11;
         C[sq * XLD + sp] = o11;
       }
-      // Q <- Q J on the column-major Q: item (pair k, rows 4 r4 .. 4 r4 + 3)
+      // Q <- Q J on the column-major Q: item (pair k, rows 4 r4 .. 4 r4 + 3).  Items are
+      // dealt from the last update thread down, so the warps holding a third Gram block
+      // (the first ones) take two items and the last two warps three.
       constexpr int R4 = W2 / 4;
-      for (int it = tid; it < NP * R4; it += NU) {
+      for (int it = NU - 1 - tid; it < NP * R4; it += NU) {
         const int k = it / R4, r4 = it % R4;
-        if (!s.rot[sl][k]) continue;
-        const float c = s.cs[sl][2 * k], sn = s.cs[sl][2 * k + 1];
+        const float2 ck = cs2[k];
+        if (ck.y == 0.f) continue;
+        const float c = ck.x, sn = ck.y;
         float4 *qi = reinterpret_cast<float4 *>(&s.Q[k * W2]) + r4;
         float4 *qj = reinterpret_cast<float4 *>(&s.Q[(NP + ((k + step) & 31)) * W2]) + r4;
         const float4 x = *qi, y = *qj;
