@@ -966,6 +966,42 @@ __device__ __forceinline__ void cross_angle(SmemTc &s, int sl, int k, float a, f
   s.rot[sl][k] = rot;
 }
 
+// Block (p, q), p <= q, of the c-th non-hand-over block of the 32 x 32 pair grid in row
+// order (the hand-over blocks (k, k + 1) and (0, 31) removed): row 0 holds 30 of them,
+// row p in 1..30 holds 31 - p, row 31 one.
+__device__ __forceinline__ void cross_block(int c, int &p, int &q) {
+  p = 0;
+  int cnt = 30;
+  while (c >= cnt) {
+    c -= cnt;
+    ++p;
+    cnt = p <= 30 ? 31 - p : 1;
+  }
+  if (p == 0)
+    q = c == 0 ? 0 : c + 1;
+  else if (p <= 30)
+    q = c == 0 ? p : p + 1 + c;
+  else
+    q = 31;
+}
+
+// Q <- Q J of a cross step on the column-major Q, item `it` = (pair k, rows 4 r4 .. 4 r4 +
+// 3): columns k and 32 + (k + step) mod 32, one 16-byte load and store per column.
+__device__ __forceinline__ void cross_q_item(SmemTc &s, const float2 *cs2, int it, int step) {
+  constexpr int W2 = SmemTc::W2, R4 = W2 / 4;
+  const int k = it / R4, r4 = it % R4;
+  const float2 ck = cs2[k];
+  if (ck.y == 0.f) return;
+  const float c = ck.x, sn = ck.y;
+  float4 *qi = reinterpret_cast<float4 *>(&s.Q[k * W2]) + r4;
+  float4 *qj = reinterpret_cast<float4 *>(&s.Q[(W2 / 2 + ((k + step) & 31)) * W2]) + r4;
+  const float4 x = *qi, y = *qj;
+  *qi = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z,
+                    c * x.w - sn * y.w);
+  *qj = make_float4(sn * x.x + c * y.x, sn * x.y + c * y.y, sn * x.z + c * y.z,
+                    sn * x.w + c * y.w);
+}
+
 // One cross inner sweep of the tensor-core worker: every pair of a local column i < 32 with
 // a local column 32 + j, in 32 steps (step t pairs column k with column 32 + (k + t) mod 32),
 // on the quadrant storage X3 (A = I x I, B = I x J, C = J x J), accumulating the rotations
@@ -987,7 +1023,15 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
   constexpr int NB = NP * (NP + 1) / 2;
   constexpr int AW = NT / 32 - 1;          // the angle warp
   constexpr int NU = NT - 32;              // update threads
-  constexpr int BPT = (NB + NU - 1) / NU;
+  constexpr int BPT = 3;
+  constexpr int NOWN = NB - NP;            // blocks of the update threads
+  // work split per step (the cost of a block is about three Q items): warps 0..4 take two
+  // blocks and three Q items, warps 5 and 6 two or three blocks and no Q item, the angle
+  // warp its hand-over block, the rotations and one Q item
+  constexpr int QW = 5 * 32;               // update threads that rotate Q
+  constexpr int XT = 5 * 32;               // first update thread with a third block
+  static_assert(2 * NU + (NOWN - 2 * NU) == NOWN && NOWN - 2 * NU <= NU - XT, "block split");
+  static_assert(3 * QW + 32 == NP * (W2 / 4), "Q item split");
   float *A = s.X3[0], *B = s.X3[1], *C = s.X3[2];
   const float tolf = (float)tol, tol2f = (float)(tol * tol);
   const int warp = tid >> 5, lane = tid & 31;
@@ -1006,26 +1050,15 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
   if (first) {
     for (int idx = tid; idx < W2 * W2; idx += NT) s.Q[idx] = (idx / W2 == idx % W2) ? 1.f : 0.f;
   }
-  // update threads: blocks of the packed upper triangle of the NP x NP block grid, except
-  // the angle warp's blocks (k, k + 1) and (0, NP - 1)
+  // update threads: blocks tid, tid + NU and (threads XT ..) 2 NU + tid - XT of the
+  // non-hand-over blocks
   int bp[BPT], bq[BPT];
 #pragma unroll
   for (int t = 0; t < BPT; ++t) {
-    const int blk = tid + t * NU;
+    const int c = t < 2 ? tid + t * NU : 2 * NU + (tid - XT);
     bp[t] = -1;
     bq[t] = 0;
-    if (warp != AW && blk < NB) {
-      int pp = 0, start = 0;
-      while (start + (NP - pp) <= blk) {
-        start += NP - pp;
-        ++pp;
-      }
-      const int qq = pp + (blk - start);
-      if (qq != pp + 1 && !(pp == 0 && qq == NP - 1)) {
-        bp[t] = pp;
-        bq[t] = qq;
-      }
-    }
+    if (warp != AW && (t < 2 || (tid >= XT && c < NOWN))) cross_block(c, bp[t], bq[t]);
   }
   // angle warp: lane k owns block (hp, hq) and forms pair k's rotations; the entry it
   // needs is o01 of (k, k + 1) or o10 of (0, NP - 1)
@@ -1092,24 +1125,11 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
         C[sp * XLD + sq] = o11;
         C[sq * XLD + sp] = o11;
       }
-      // Q <- Q J on the column-major Q: item (pair k, rows 4 r4 .. 4 r4 + 3).  Items are
-      // dealt from the last update thread down, so the warps holding a third Gram block
-      // (the first ones) take two items and the last two warps three.
-      constexpr int R4 = W2 / 4;
-      for (int it = NU - 1 - tid; it < NP * R4; it += NU) {
-        const int k = it / R4, r4 = it % R4;
-        const float2 ck = cs2[k];
-        if (ck.y == 0.f) continue;
-        const float c = ck.x, sn = ck.y;
-        float4 *qi = reinterpret_cast<float4 *>(&s.Q[k * W2]) + r4;
-        float4 *qj = reinterpret_cast<float4 *>(&s.Q[(NP + ((k + step) & 31)) * W2]) + r4;
-        const float4 x = *qi, y = *qj;
-        *qi = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z,
-                          c * x.w - sn * y.w);
-        *qj = make_float4(sn * x.x + c * y.x, sn * x.y + c * y.y, sn * x.z + c * y.z,
-                          sn * x.w + c * y.w);
-      }
+      if (tid < QW)
+        for (int u = 0; u < 3; ++u) cross_q_item(s, cs2, tid + u * QW, step);
     }
+    if (warp == AW) cross_q_item(s, reinterpret_cast<const float2 *>(s.cs[sl]), 3 * QW + lane,
+                                 step);
     bar.sync();
   }
 }
