@@ -74,6 +74,10 @@ CASES_I = [
     ("tall64", (150, 70, 4), torch.float64, 10),
     ("one_slice", (33, 20, 1), torch.float32, 20),
     ("rankdef", (80, 40, 3), torch.float32, 4),
+    # 16 column blocks (a ragged last one): 14 of the 15 rounds of a sweep are cross sweeps
+    ("blocks16", (520, 500, 2), torch.float32, 40),
+    # 60 columns exactly zero in every slice: pairs that never rotate, rank 80
+    ("zerocols", (150, 140, 2), torch.float32, 12),
 ]
 
 
@@ -87,6 +91,8 @@ def _case_input(name, shape, seed=3):
         X = synth.cp_tensor(n1, n2, n3, 5, rng, noise_rel=0.0)
     else:
         X = synth.cp_tensor(n1, n2, n3, min(n1, n2) // 2, rng, noise_rel=1e-2)
+    if name == "zerocols":
+        X[:, 40:100, :] = 0.0
     return X, synth.dct2_matrix(n3)
 
 
