@@ -1014,8 +1014,9 @@ __device__ __forceinline__ void cross_q_item(SmemTc &s, const float2 *cs2, int i
 // next step's pair k joins column k with the J column of pair k + 1, so its cross entry is
 // in block (k, k + 1) (block (0, 31) for k = 31).  Lane k of the last warp owns that block:
 // it rotates it and forms pair k's next rotation from the entry it has just computed, while
-// the other warps rotate the remaining blocks and Q.  One barrier per step.  With row
-// stride 33 the loads and stores of a warp's blocks fall on distinct banks.
+// the other warps rotate the remaining blocks and most of Q (the split below balances the
+// warps).  One barrier per step.  With row stride 33 the loads and stores of a warp's
+// blocks fall on distinct banks.
 __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
                                   const GroupBar &bar) {
   constexpr int W2 = SmemTc::W2;
