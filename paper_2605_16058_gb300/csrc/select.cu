@@ -1,16 +1,24 @@
 // t-SVDM-II rank choice (Algorithm 2, steps 2-8) on the device.
 //
-// Input: each slice's singular values, sorted descending (cols x nslices).
-//   v = every sigma^2 (FP64), sorted ascending by an LSD radix sort of order-preserving
-//   keys: for FP32 the bits of sigma itself (sigma^2 of an FP32 value is exact in FP64,
-//   so the order and the ties of sigma and sigma^2 agree), for FP64 the bits of sigma^2;
-//   w = the running FP64 sums of v in sorted order (block-wide scans, fixed order);
-//   J = #{l : w_l / sum(v) < eps^2} (w is non-decreasing, so this is the largest such l);
-//   tau = v_J; rho_i = #{j : sigma_{j,i}^2 > tau} (values equal to tau are dropped);
-//   offsets = exclusive prefix sum of rho (int64).
-// The whole selection runs in one CTA of 1024 threads: the key count is n3 min(n1, n2)
-// (a few hundred thousand at most for the workloads here), so it is latency-bound and a
-// single CTA with block-wide scans keeps it deterministic.
+// Input: each slice's singular values, sorted descending (cols x nslices).  Algorithm 2
+// sorts all v = sigma^2 ascending, takes the running sums w, J = #{l : w_l < eps^2 sum(v)}
+// (the largest such l, w being non-decreasing), tau = v_J, and keeps in slice i the
+// rho_i = #{j : sigma_{j,i}^2 > tau} values above tau (so every copy of tau is dropped).
+//
+// The sort is not needed for tau.  With S(k) = the sum of all values whose key is below k
+// (keys: the bits of sigma for FP32, of sigma^2 for FP64; both order like the values), the
+// first copy of a value x is included in J exactly when S(x) + x < eps^2 sum(v); the left
+// side only grows with x, so tau is the largest present value x with S(x) + x below the
+// limit.  Here:
+//   1. per slice, the FP64 sums of sigma^2 over each tail j..cols-1 (ascending order is the
+//      tail of the descending slice), and their total;
+//   2. a bisection over the key bits for the largest key k with S(k) + val(k) < limit, where
+//      S(k) adds each slice's tail below k (binary search in the sorted slice);
+//   3. tau = the largest present key <= k; rho_i, the discarded sum and the offsets
+//      (exclusive prefix sum of rho, int64) from one binary search per slice.
+// All sums are FP64 in a fixed order, so a result is reproducible run to run; against the
+// sorted running sum of Algorithm 2 it differs only by FP64 summation order.  One CTA per
+// selection: the work is a few hundred slices times ~32 bisection steps of a binary search.
 #include "common.cuh"
 
 namespace tsvdm {
@@ -34,39 +42,8 @@ template <> struct KeyOf<double> {
   __device__ static double val(K k) { return __longlong_as_double((long long)k); }
 };
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
-// Block-wide inclusive scan of one double per thread, fixed order. Returns the inclusive
-// value; *total receives the block sum.
-__device__ double block_scan(double v, double *wsum, double *total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    double u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += u;
-  }
-  if (lane == 31) wsum[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    double x = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      double u = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += u;
-    }
-    wsum[lane] = x;
-  }
-  __syncthreads();
-  if (warp > 0) v += wsum[warp - 1];
-  *total = wsum[NW - 1];
-  __syncthreads();
-  return v;
-}
-
+// Block-wide inclusive scan of one int64 per thread, fixed order; *total receives the
+// block sum.
 __device__ long long block_scan_ll(long long v, long long *wsum, long long *total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -92,118 +69,154 @@ __device__ long long block_scan_ll(long long v, long long *wsum, long long *tota
   return v;
 }
 
+// Fixed-order block reduction of one double per thread (every thread gets the sum).
+__device__ double block_sum(double v, double *wsum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < NW; ++w) t += wsum[w];
+  __syncthreads();
+  return t;
+}
+
+template <typename K>
+__device__ K block_max(K v, K *wk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const K u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  if (lane == 0) wk[warp] = v;
+  __syncthreads();
+  K t = wk[0];
+  for (int w = 1; w < NW; ++w) t = wk[w] > t ? wk[w] : t;
+  __syncthreads();
+  return t;
+}
+
+// First index j of the descending slice s with key(s[j]) < k (cols if none).
+template <typename T>
+__device__ __forceinline__ int first_below(const T *s, int cols, typename KeyOf<T>::K k) {
+  int lo = 0, hi = cols;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (KeyOf<T>::key(s[mid]) >= k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 template <typename T>
 __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, double eps,
                             void *kws, double *scal, int *ranks, int64_t *offsets) {
   using KO = KeyOf<T>;
   using K = typename KO::K;
-  __shared__ int wc[NW * 256];
-  __shared__ int base_off[256];
-  __shared__ int tile_cnt[256];
+  // key of +inf: no finite singular value reaches it
+  constexpr K KINF = sizeof(K) == 4 ? K(0x7f800000u) : K(0x7ff0000000000000ull);
   __shared__ double wsum[NW];
   __shared__ long long wsum_ll[NW];
-  __shared__ K s_tau;
-  __shared__ int s_has_tau;
+  __shared__ K wkey[NW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t N = (int64_t)cols * nslices;
-  K *buf0 = reinterpret_cast<K *>(kws);
-  K *buf1 = buf0 + N;
-
-  for (int64_t e = tid; e < N; e += ST) buf0[e] = KO::key(sig[e]);
-  __syncthreads();
-
-  // LSD radix sort, 8-bit digits, stable
-  K *src = buf0, *dst = buf1;
-  for (int pass = 0; pass < (int)sizeof(K); ++pass) {
-    const int sh = 8 * pass;
-    if (tid < 256) base_off[tid] = 0;
-    __syncthreads();
-    for (int64_t e = tid; e < N; e += ST) atomicAdd(&base_off[(int)((src[e] >> sh) & 255)], 1);
-    __syncthreads();
-    if (tid == 0) {
-      int run = 0;
-      for (int d = 0; d < 256; ++d) {
-        int c = base_off[d];
-        base_off[d] = run;
-        run += c;
-      }
+  // tail[i * cols + j] = sum of sigma_{j',i}^2 for j' >= j (the cols - j smallest of slice i)
+  double *tail = reinterpret_cast<double *>(kws);
+  double part = 0.0;
+  for (int i = tid; i < nslices; i += ST) {
+    const T *s = sig + (int64_t)i * cols;
+    double *t = tail + (int64_t)i * cols;
+    double run = 0.0;
+    for (int j = cols - 1; j >= 0; --j) {
+      run += KO::val(KO::key(s[j]));
+      t[j] = run;
     }
-    __syncthreads();
-    for (int64_t b0 = 0; b0 < N; b0 += ST) {
-      const int64_t e = b0 + tid;
-      const bool valid = e < N;
-      const K key = valid ? src[e] : K(0);
-      const int d = valid ? (int)((key >> sh) & 255) : 256;
-      for (int x = tid; x < NW * 256; x += ST) wc[x] = 0;
-      __syncthreads();
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      const int rk = __popc(peers & lanemask_lt());
-      if (valid && rk == 0) wc[warp * 256 + d] = __popc(peers);
-      __syncthreads();
-      if (tid < 256) {
-        int run = 0;
-        for (int w = 0; w < NW; ++w) {
-          int c = wc[w * 256 + tid];
-          wc[w * 256 + tid] = run;
-          run += c;
-        }
-        tile_cnt[tid] = run;
-      }
-      __syncthreads();
-      if (valid) dst[base_off[d] + wc[warp * 256 + d] + rk] = key;
-      __syncthreads();
-      if (tid < 256) base_off[tid] += tile_cnt[tid];
-      __syncthreads();
+    part += run;
+  }
+  const double total = block_sum(part, wsum);
+  const double limit = eps * eps * total;
+  bool has_tau = false;
+  K tau = K(0);
+  if (total == 0.0) {
+    has_tau = true;                  // an all-zero spectrum keeps nothing
+    tau = ~K(0);
+  } else if (eps * eps >= 1.0) {
+    // w_N = sum(v) exactly, so eps^2 > 1 discards every value and eps^2 = 1 all but the
+    // last one in sorted order: tau is the largest value, or the second largest counting
+    // copies (decided here without any sum, so the boundary w_N is exact)
+    K m1 = K(0);
+    for (int i = tid; i < nslices; i += ST) {
+      const K k0 = KO::key(sig[(int64_t)i * cols]);
+      m1 = k0 > m1 ? k0 : m1;
     }
-    K *t = src;
-    src = dst;
-    dst = t;
-  }
-  // src holds the keys in ascending order.
-
-  // pass 1: total = w_N (same blocked scan as pass 2, so w_N == total exactly)
-  double carry = 0.0, tot;
-  for (int64_t b0 = 0; b0 < N; b0 += ST) {
-    int64_t e = b0 + tid;
-    double v = e < N ? KO::val(src[e]) : 0.0;
-    block_scan(v, wsum, &tot);
-    carry += tot;
-  }
-  const double total = carry;
-  // pass 2: J = #{l : w_l / total < eps^2}
-  const double eps2 = eps * eps;
-  long long Jc = 0;
-  carry = 0.0;
-  if (total > 0.0) {
-    for (int64_t b0 = 0; b0 < N; b0 += ST) {
-      int64_t e = b0 + tid;
-      double v = e < N ? KO::val(src[e]) : 0.0;
-      double w = block_scan(v, wsum, &tot) + carry;
-      carry += tot;
-      int ok = (e < N) && (w / total < eps2);
-      Jc += __syncthreads_count(ok);
-    }
-  }
-  if (tid == 0) {
-    if (total == 0.0) {
-      s_has_tau = 1;          // an all-zero spectrum keeps nothing
-      s_tau = ~K(0);
-    } else if (Jc > 0) {
-      s_has_tau = 1;
-      s_tau = src[Jc - 1];
+    m1 = block_max<K>(m1, wkey);
+    if (eps * eps > 1.0) {
+      has_tau = true;
+      tau = m1;
     } else {
-      s_has_tau = 0;          // J = 0: nothing is discarded
-      s_tau = K(0);
+      double copies = 0.0;
+      K second = K(0);
+      int found = 0;
+      for (int i = tid; i < nslices; i += ST) {
+        const T *s = sig + (int64_t)i * cols;
+        const int c = first_below(s, cols, m1);         // copies of the largest value
+        copies += (double)c;
+        if (c < cols) {
+          const K kc = KO::key(s[c]);
+          if (!found || kc > second) second = kc;
+          found = 1;
+        }
+      }
+      copies = block_sum(copies, wsum);
+      found = __syncthreads_or(found);
+      second = block_max<K>(second, wkey);
+      if (copies >= 2.0) {
+        has_tau = true;
+        tau = m1;
+      } else {
+        has_tau = found != 0;
+        tau = second;
+      }
     }
+  } else if (limit > 0.0) {
+    // largest key k with S(k) + val(k) < limit: true at k = 0, false at +inf
+    K lo = 0, hi = KINF;
+    while (hi - lo > 1) {
+      const K mid = lo + (hi - lo) / 2;
+      double below = 0.0;
+      for (int i = tid; i < nslices; i += ST) {
+        const int c = first_below(sig + (int64_t)i * cols, cols, mid);
+        if (c < cols) below += tail[(int64_t)i * cols + c];
+      }
+      const double S = block_sum(below, wsum);
+      if (S + KO::val(mid) < limit)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    // tau = the largest present key <= lo (none: J = 0, nothing is discarded)
+    K best = K(0);
+    int found = 0;
+    for (int i = tid; i < nslices; i += ST) {
+      const T *s = sig + (int64_t)i * cols;
+      const int c = first_below(s, cols, lo + 1);       // first key <= lo
+      if (c < cols) {
+        const K kc = KO::key(s[c]);
+        if (!found || kc > best) best = kc;
+        found = 1;
+      }
+    }
+    found = __syncthreads_or(found);
+    best = block_max<K>(best, wkey);
+    has_tau = found != 0;
+    tau = best;
   }
-  __syncthreads();
-  const bool has_tau = s_has_tau;
-  const K tau = s_tau;
-  // ranks: each slice's keys are in descending order -> binary search
+  // ranks (values above tau), their offsets and the discarded sum
   long long carry_ll = 0, tot_ll;
   double disc = 0.0;
   for (int b0 = 0; b0 < nslices; b0 += ST) {
-    int i = b0 + tid;
+    const int i = b0 + tid;
     long long r = 0;
     if (i < nslices) {
       const T *s = sig + (int64_t)i * cols;
@@ -212,35 +225,25 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
       } else if (total == 0.0) {
         r = 0;
       } else {
-        int lo = 0, hi = cols;      // first j with key(s[j]) <= tau
-        while (lo < hi) {
-          int mid = (lo + hi) >> 1;
-          if (KO::key(s[mid]) > tau) lo = mid + 1;
-          else hi = mid;
-        }
-        r = lo;
+        r = tau == ~K(0) ? 0 : first_below(s, cols, tau + 1);   // first key <= tau
+        if (r < cols) disc += tail[(int64_t)i * cols + r];
       }
-      for (int j = (int)r; j < cols; ++j) disc += KO::val(KO::key(s[j]));
       ranks[i] = (int)r;
     }
     long long incl = block_scan_ll(r, wsum_ll, &tot_ll);
     if (i < nslices) offsets[i] = carry_ll + incl - r;
     carry_ll += tot_ll;
   }
-  // discarded sum (fixed-order block reduction)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) disc += __shfl_xor_sync(0xffffffffu, disc, o);
-  if (lane == 0) wsum[warp] = disc;
-  __syncthreads();
+  const double d = block_sum(disc, wsum);
   if (tid == 0) {
-    double d = 0.0;
-    for (int w = 0; w < NW; ++w) d += wsum[w];
     offsets[nslices] = carry_ll;
     scal[SC_TOTAL] = total;
     scal[SC_DISCARD] = total > 0.0 ? d : 0.0;
     scal[SC_TAU] = (has_tau && total > 0.0) ? KO::val(tau) : -1.0;
     scal[SC_TOTRANK] = (double)carry_ll;
   }
+  (void)lane;
+  (void)warp;
 }
 
 // t-SVDM-I truncation sums: total = sum of all sigma^2, discarded = sum over j >= k.
