@@ -7,13 +7,13 @@
 //
 // The sort is not needed for tau.  With S(k) = the sum of all values whose key is below k
 // (keys: the bits of sigma for FP32, of sigma^2 for FP64; both order like the values), the
-// first copy of a value x is included in J exactly when S(x) + x < eps^2 sum(v); the left
-// side only grows with x, so tau is the largest present value x with S(x) + x below the
-// limit.  Here:
+// first copy of a value x is included in J exactly when (S(x) + x) / sum(v) < eps^2; the
+// left side only grows with x, so tau is the largest present value x for which it holds.
+// Here:
 //   1. per slice, the FP64 sums of sigma^2 over each tail j..cols-1 (ascending order is the
 //      tail of the descending slice), and their total;
-//   2. a bisection over the key bits for the largest key k with S(k) + val(k) < limit, where
-//      S(k) adds each slice's tail below k (binary search in the sorted slice);
+//   2. a bisection over the key bits for the largest key k with (S(k) + val(k)) / sum(v)
+//      < eps^2, where S(k) adds each slice's tail below k (binary search in the slice);
 //   3. tau = the largest present key <= k; rho_i, the discarded sum and the offsets
 //      (exclusive prefix sum of rho, int64) from one binary search per slice.
 // All sums are FP64 in a fixed order, so a result is reproducible run to run; against the
@@ -135,13 +135,14 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
     part += run;
   }
   const double total = block_sum(part, wsum);
-  const double limit = eps * eps * total;
+  const double eps2 = eps * eps;
   bool has_tau = false;
   K tau = K(0);
   if (total == 0.0) {
     has_tau = true;                  // an all-zero spectrum keeps nothing
     tau = ~K(0);
-  } else if (eps * eps >= 1.0) {
+  } else if (eps2 >= 1.0) {
+    // (the entry points take eps in (0, 1); this keeps the kernel exact for any eps)
     // w_N = sum(v) exactly, so eps^2 > 1 discards every value and eps^2 = 1 all but the
     // last one in sorted order: tau is the largest value, or the second largest counting
     // copies (decided here without any sum, so the boundary w_N is exact)
@@ -151,7 +152,7 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
       m1 = k0 > m1 ? k0 : m1;
     }
     m1 = block_max<K>(m1, wkey);
-    if (eps * eps > 1.0) {
+    if (eps2 > 1.0) {
       has_tau = true;
       tau = m1;
     } else {
@@ -179,8 +180,9 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
         tau = second;
       }
     }
-  } else if (limit > 0.0) {
-    // largest key k with S(k) + val(k) < limit: true at k = 0, false at +inf
+  } else if (eps2 > 0.0) {
+    // largest key k with (S(k) + val(k)) / total < eps^2 (Algorithm 2's own comparison):
+    // true at k = 0, false at +inf
     K lo = 0, hi = KINF;
     while (hi - lo > 1) {
       const K mid = lo + (hi - lo) / 2;
@@ -190,7 +192,7 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
         if (c < cols) below += tail[(int64_t)i * cols + c];
       }
       const double S = block_sum(below, wsum);
-      if (S + KO::val(mid) < limit)
+      if ((S + KO::val(mid)) / total < eps2)
         lo = mid;
       else
         hi = mid;

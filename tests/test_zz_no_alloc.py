@@ -68,3 +68,48 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     offs = torch.zeros(5, dtype=torch.int64, device="cuda")
     assert _noalloc(sig, 1024, 300, 0.1, ranks, offs, None) == native.ESCRATCH
     assert _noalloc(sig, 4, 1, 1.5, ranks, offs, None) == native.EINVAL
+
+
+def _spectra():
+    """Singular values (cols x nslices, descending per slice) whose squares and running
+    sums are exact in FP64 (small integers: ties, zeros, exact boundaries), plus random
+    ones."""
+    out = [np.array([[3, 3, 2], [3, 2, 2], [2, 2, 2], [1, 0, 1]], dtype=np.float64),
+           np.array([[5, 4], [1, 4], [1, 0], [0, 0]], dtype=np.float64),
+           np.array([[2], [1], [1], [1]], dtype=np.float64),
+           np.array([[7, 1, 1, 1]], dtype=np.float64)]
+    rng = np.random.default_rng(40)
+    for _ in range(6):
+        cols, ns = int(rng.integers(1, 40)), int(rng.integers(1, 30))
+        S = np.exp(rng.normal(0.0, 2.0, (cols, ns))).astype(np.float32).astype(np.float64)
+        out.append(-np.sort(-S, axis=0))
+    big = rng.integers(0, 6, (300, 40)).astype(np.float64)        # many ties
+    out.append(-np.sort(-big, axis=0))
+    return out
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.25, 0.5, 0.75, 0.999])
+def test_noalloc_selection_matches_algorithm2_on_exact_spectra(eps):
+    """Ranks, offsets, the total rank and tau equal Algorithm 2 (the oracle's sort and
+    cumulative sum) exactly; the discarded energy to FP64 summation order."""
+    import oracle
+    from paper_2605_16058_gb300 import native
+    for S in _spectra():
+        cols, ns = S.shape
+        want = oracle.select_ranks(S, eps)
+        sig = torch.tensor(np.ascontiguousarray(S.T).astype(np.float32), device="cuda")
+        ranks = torch.full((ns,), -1, dtype=torch.int32, device="cuda")
+        offs = torch.full((ns + 1,), -1, dtype=torch.int64, device="cuda")
+        summ = torch.zeros(4, dtype=torch.float64, device="cuda")
+        assert _noalloc(sig, cols, ns, eps, ranks, offs, summ) == native.OK
+        torch.cuda.synchronize()
+        assert np.array_equal(ranks.cpu().numpy(), want["ranks"]), (S.T, eps)
+        assert np.array_equal(offs.cpu().numpy(), oracle.offsets_from_ranks(want["ranks"]))
+        total, disc, tau, totrank = summ.cpu().tolist()
+        assert int(totrank) == int(np.sum(want["ranks"]))
+        assert abs(total - want["total"]) <= 1e-13 * want["total"]
+        assert abs(disc - want["discarded"]) <= 1e-13 * want["total"]
+        if want["J"] > 0:
+            assert tau == want["tau"]
+        else:
+            assert tau == -1.0
