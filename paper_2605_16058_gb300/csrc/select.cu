@@ -120,7 +120,7 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
   __shared__ double wsum[NW];
   __shared__ long long wsum_ll[NW];
   __shared__ K wkey[NW];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   // tail[i * cols + j] = sum of sigma_{j',i}^2 for j' >= j (the cols - j smallest of slice i)
   double *tail = reinterpret_cast<double *>(kws);
   double part = 0.0;
@@ -244,8 +244,6 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
     scal[SC_TAU] = (has_tau && total > 0.0) ? KO::val(tau) : -1.0;
     scal[SC_TOTRANK] = (double)carry_ll;
   }
-  (void)lane;
-  (void)warp;
 }
 
 // t-SVDM-I truncation sums: total = sum of all sigma^2, discarded = sum over j >= k.
