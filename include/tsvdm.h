@@ -272,7 +272,7 @@ typedef enum {
   TSVDM_STAGE_TRANSPOSE = 1,  /* slice transposition for n1 < n2                     */
   TSVDM_STAGE_JACOBI = 2,     /* batched one-sided Jacobi sweeps                     */
   TSVDM_STAGE_FINALIZE = 3,   /* column norms and per-slice descending order         */
-  TSVDM_STAGE_SELECT = 4,     /* t-SVDM-II sort, FP64 prefix sums, ranks, offsets    */
+  TSVDM_STAGE_SELECT = 4,     /* t-SVDM-II threshold (tail sums), ranks, offsets     */
   TSVDM_STAGE_EMIT = 5,       /* normalised, sign-fixed factor output / packing      */
   TSVDM_STAGE_OTHER = 6,      /* reductions, products and small kernels              */
   TSVDM_STAGE_COUNT = 7
@@ -354,7 +354,7 @@ tsvdm_status tsvdm_batch_graph_kernels(tsvdm_batch b, int64_t *kernels);
  * another allocator up front, or a service that forbids allocation on its request path
  * because a driver allocation can synchronise the device and take milliseconds).
  * Same computation as the selection inside tsvdm_tolerance: Algorithm 2 steps 2-8 on
- * given singular values, with the sort scratch in a fixed 2 MiB array built into the
+ * given singular values, with its scratch in a fixed 2 MiB array built into the
  * library (held on every GPU that loads it until the process exits) instead of a plan.
  *   sigma    device float [cols x nslices], column i = slice i's singular values sorted
  *            in descending order (e.g. S of tsvdm_fixed_rank with k = min(n1, n2))

@@ -73,7 +73,7 @@ struct tsvdm_batch_s {
   int *iarena = nullptr;        // perm, ranks
   float *farena = nullptr;      // norm2
   int64_t *larena = nullptr;    // offsets
-  unsigned long long *karena = nullptr;   // sort keys
+  unsigned long long *karena = nullptr;   // selection scratch (FP64 tail sums)
   double *darena = nullptr;     // scalars
   SliceDesc *desc = nullptr;    // device
   SelectSeg *segs = nullptr;    // device

@@ -1,5 +1,5 @@
 // Allocation-free entry point: the t-SVDM-II rank choice (the same device selection kernel
-// that tsvdm_tolerance runs) with its sort scratch in a fixed, file-scope device array
+// that tsvdm_tolerance runs) with its scratch in a fixed, file-scope device array
 // instead of a plan's workspace.
 //
 // Who needs it: callers that must not call cudaMalloc.  Examples are a process that hands
@@ -8,10 +8,10 @@
 // their request path because a driver allocation can synchronise the device and take
 // milliseconds.  Such callers already hold the singular values and the output buffers.
 //
-// The scratch (2 MiB of sort keys plus a few FP64 scalars) is part of the library image:
-// every GPU that loads the library holds it until the process exits.  Every call shares
-// it, so calls whose kernels overlap on the GPU (different streams, or several host
-// threads) race on it; serialise them on one stream.
+// The scratch (2 MiB: one FP64 tail sum per singular value, plus a few FP64 scalars) is
+// part of the library image: every GPU that loads the library holds it until the process
+// exits.  Every call shares it, so calls whose kernels overlap on the GPU (different
+// streams, or several host threads) race on it; serialise them on one stream.
 #include <mutex>
 
 #include "common.cuh"
@@ -21,7 +21,7 @@ namespace {
 constexpr int64_t NOALLOC_MAX_VALUES = 262144;      // sigma values (cols * nslices) per call
 constexpr int MAX_DEVICES = 64;
 
-static __device__ __align__(256) unsigned int g_select_keys[2 * NOALLOC_MAX_VALUES];
+static __device__ __align__(256) double g_select_scratch[NOALLOC_MAX_VALUES];
 static __device__ __align__(256) double g_select_scal[tsvdm::SC_COUNT];
 
 struct DeviceScratch {
@@ -43,7 +43,7 @@ tsvdm_status scratch_for_current_device(DeviceScratch *out) {
   DeviceScratch &d = g_scratch[dev];
   if (!d.ready) {
     void *k = nullptr, *s = nullptr;
-    if (cudaGetSymbolAddress(&k, g_select_keys) != cudaSuccess) return TSVDM_ECUDA;
+    if (cudaGetSymbolAddress(&k, g_select_scratch) != cudaSuccess) return TSVDM_ECUDA;
     if (cudaGetSymbolAddress(&s, g_select_scal) != cudaSuccess) return TSVDM_ECUDA;
     d.keys = k;
     d.scal = (double *)s;

@@ -3,7 +3,7 @@ existing entry point tsvdm_tolerance, through the C ABI, on two calls in a row.
 
 The allocation-free entry point serves callers that must not call cudaMalloc (a process
 whose device memory is all handed to another allocator, or a request path that forbids
-driver allocations); it keeps its sort scratch in a fixed array inside the library.
+driver allocations); it keeps its scratch in a fixed array inside the library.
 Ranks and offsets are integers and must match exactly; the reported error within 1e-12.
 """
 import ctypes
