@@ -77,7 +77,9 @@ def _spectra():
     out = [np.array([[3, 3, 2], [3, 2, 2], [2, 2, 2], [1, 0, 1]], dtype=np.float64),
            np.array([[5, 4], [1, 4], [1, 0], [0, 0]], dtype=np.float64),
            np.array([[2], [1], [1], [1]], dtype=np.float64),
-           np.array([[7, 1, 1, 1]], dtype=np.float64)]
+           np.array([[7, 1, 1, 1]], dtype=np.float64),
+           # golden case C: at eps = 0.25 the running sum meets eps^2 sum(v) exactly
+           np.array([[1, 3], [1, 2], [0, 1]], dtype=np.float64)]
     rng = np.random.default_rng(40)
     for _ in range(6):
         cols, ns = int(rng.integers(1, 40)), int(rng.integers(1, 30))
