@@ -161,3 +161,40 @@ def test_cayley_factors_swapped_is_caught(monkeypatch):
 
     monkeypatch.setattr(oracle, "cayley", cayley)
     assert _fails(pins.test_cayley_is_orthogonal_and_starts_at_m0)
+
+
+# ---------------------------------------------------------------- back-transform (Sec. 2.2)
+def test_reconstruction_through_the_transposed_inverse_is_caught(monkeypatch):
+    real = oracle.reconstruct
+
+    def reconstruct(U, S, V, Minv, k=None, offsets=None):
+        if not isinstance(Minv, (list, tuple)):
+            Minv = np.ascontiguousarray(np.asarray(Minv).T)    # M instead of M^{-1}
+        return real(U, S, V, Minv, k=k, offsets=offsets)
+
+    monkeypatch.setattr(oracle, "reconstruct", reconstruct)
+    assert _fails(pins.test_full_rank_reconstruction_is_exact)
+
+
+def test_original_domain_factor_missing_a_mode_is_caught(monkeypatch):
+    real = oracle.original_domain
+
+    def original_domain(F, Minv):
+        if isinstance(Minv, (list, tuple)):                    # the last mode left out
+            Minv = list(Minv[:-1]) + [np.eye(np.asarray(Minv[-1]).shape[0])]
+        return real(F, Minv)
+
+    monkeypatch.setattr(oracle, "original_domain", original_domain)
+    assert _fails(pins.test_dway_original_domain_factors_rebuild_x)
+
+
+# ---------------------------------------------------------------- data-driven M (Sec. 2.2)
+def test_data_driven_transform_transposed_is_caught(monkeypatch):
+    real = oracle.data_transform
+
+    def data_transform(X):
+        M, sig = real(X)
+        return M.T.copy(), sig                                 # columns, not rows
+
+    monkeypatch.setattr(oracle, "data_transform", data_transform)
+    assert _fails(pins.test_data_transform_diagonalises_the_mode3_gram)
