@@ -133,6 +133,17 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' values of x (the slowest rank sets the job's time); x
+    itself when there is one rank (dist is None)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def jacobi_traffic_per_slice():
     """DRAM bytes per slice of the Jacobi kernel from the committed ncu summary, or None
     when the kernel source changed since those counters were taken."""
@@ -443,11 +454,7 @@ def main():
     if dist:
         dist.barrier()
     clocks = clk.stop()
-    ms_step = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     sweeps, rots = native.tsvdm_plan_stats(plan.handle)
     native.tsvdm_plan_profile(plan.handle, 0)
     in_bytes = n1 * n2 * n3 * 4
@@ -470,11 +477,7 @@ def main():
         for _ in range(args.steps):
             tot_h, _, _ = native.tsvdm_tolerance(plan.handle, Xh, Mh, eps, rh, oh, Uh, Sh, Vh, cap)
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
         d2h = tot_h * (n1 + n2 + 1) * 4 + n3 * 4 + (n3 + 1) * 8
         e2e = {"value": world * in_bytes / te / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": in_bytes + M.numel() * 4, "d2h_bytes_per_step": int(d2h),
