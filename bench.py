@@ -71,11 +71,45 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--angles", default="fp64", choices=["fp64", "fp32"],
+                    help="arithmetic of the slice SVDs' rotation test and angle")
+    ap.add_argument("--vectors", default="accumulate", choices=["accumulate", "second_pass"],
+                    help="singular vectors in one pass, or kept ones in a second pass")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the other configurations (all-FP64 GPU path, CFD, batch, "
+                         "the 64x48x16 FP64 case)")
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16x3"],
                     help="TTM arithmetic (the slice SVDs run in FP32 in every mode)")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="batch workload: also time the all-FP64 GPU path on the same inputs")
     return ap.parse_args()
+
+
+_PROBED = {}
+
+
+def probe_peaks():
+    """Measured FP32 / FP64 CUDA-core and TF32 / BF16 tensor-core rates of this GPU
+    (tsvdm_probe_peak: kernels that run only the unit's own instruction on every SM; best
+    of three launches each, in TFLOP/s)."""
+    if _PROBED:
+        return _PROBED
+    from paper_2605_16058_gb300 import native as N
+    for name, unit, iters in [("fp32_fma", N.PROBE_FP32_FMA, 1 << 20),
+                              ("tf32_mma", N.PROBE_TF32_MMA, 1 << 19),
+                              ("bf16_mma", N.PROBE_BF16_MMA, 1 << 19),
+                              ("fp64_fma", N.PROBE_FP64_FMA, 1 << 13)]:
+        _PROBED[name] = max(N.tsvdm_probe_peak(unit, iters) for _ in range(3))
+    return _PROBED
+
+
+def fp32_peak_tflops():
+    """The FP32 CUDA-core peak (measured by the probe once the library is loaded on a GPU)."""
+    if _PROBED:
+        return _PROBED["fp32_fma"], "measured on this GPU (FP32 FMA-loop probe, tsvdm_probe_peak)"
+    pk, _ = peaks()
+    return (SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12,
+            "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock")
 
 
 def peaks():
@@ -162,15 +196,21 @@ def jacobi_traffic_per_slice():
     return float(vals["dram_bytes_per_slice"])
 
 
-def cpu_sample(X, M, nslices, threads):
-    """The oracle (FP64, as it stands) on a bounded sample: TTM + SVD of `nslices`
-    slices spread over `threads` worker threads."""
+def spread(n, count):
+    """`count` slice indices spread evenly over 0 .. n-1 (both ends included)."""
+    import numpy as np
+    return sorted(set(int(round(x)) for x in np.linspace(0, n - 1, max(1, min(count, n)))))
+
+
+def cpu_sample(X, M, which, threads):
+    """The oracle (FP64, as it stands) on a bounded sample: TTM + SVD of the slices
+    `which`, spread over `threads` worker threads.  Returns the time and the oracle's
+    U (m x r x len(which)) and singular values (r x len(which))."""
     import oracle
-    which = list(range(nslices))
     t0 = time.perf_counter()
-    A = oracle.ttm3(X, M, which=which)
-    oracle.svd_slices(A, threads=threads)
-    return time.perf_counter() - t0
+    A = oracle.ttm3(X, M, which=list(which))
+    U, S, V, _ = oracle.svd_slices(A, threads=threads)
+    return time.perf_counter() - t0, U, S
 
 
 def batch_inputs(count):
@@ -180,16 +220,16 @@ def batch_inputs(count):
     return [(sh, synth.batch_item(i, sh)) for i, sh in enumerate(shapes)]
 
 
-def run_batch_bench(args, world, rank, local):
-    """All tensors of the batch in one CUDA graph (TTMs, one persistent Jacobi launch over
-    every slice, grouped finalize/selection, emission); value = input GB/s of the replay."""
+def batch_measure(args, local, count, fp64_compare):
+    """All `count` tensors of the batch in one CUDA graph (TTMs, one persistent Jacobi launch
+    over every slice, grouped finalize/selection, emission), autotuned; returns the figures
+    of the replay (and of the all-FP64 graph on the same inputs when fp64_compare)."""
     import numpy as np
     import torch
     from paper_2605_16058_gb300 import build, native as N
 
     build.build()
     torch.cuda.set_device(local)
-    count = 64 if args.workload == "batch" else 8
     items = batch_inputs(count)
     stream = torch.cuda.Stream()
 
@@ -224,7 +264,7 @@ def run_batch_bench(args, world, rank, local):
         return b, ios, keep
 
     def timed(b, steps, warmup):
-        for _ in range(max(3, warmup)):
+        for _ in range(warmup):
             N.tsvdm_batch_launch(b)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -241,7 +281,7 @@ def run_batch_bench(args, world, rank, local):
     choice = N.tsvdm_batch_tune(b, ios)
     N.tsvdm_batch_capture(b, ios)
     clk = Clocks(local)
-    ms = timed(b, args.steps, args.warmup)
+    ms = timed(b, args.steps, max(3, args.warmup))
     clocks = clk.stop()
     st, sweeps, rots = N.tsvdm_batch_status(b)
     alg, mp_sum = 0.0, 0.0
@@ -253,35 +293,55 @@ def run_batch_bench(args, world, rank, local):
     # algorithmic flops: dots of every executed sweep (mean sweeps per slice) plus
     # 6 (m + p) per applied rotation (slice-averaged m + p)
     alg_flops = alg * mean_sw + rots * 6.0 * mp_sum / nslices
-    pk, src = peaks()
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak, fp32_src = fp32_peak_tflops()
     rels = [float(k[7].item()) for k in keep]
-    line = {
-        "metric": METRIC, "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "slices_per_s": nslices / (ms * 1e-3), "ttm_precision": args.prec,
-        "config": {"workload": WORKLOADS[args.workload][2], "tensors": len(items),
-                   "slices": nslices, "input_bytes": in_bytes, "status": int(st),
-                   "jacobi_sweeps_mean": mean_sw, "autotuned": choice,
-                   "max_rel_err_tol_items": max(r for (sh, it), r in zip(items, rels)
-                                                if it["mode"] == "tol")},
+    out = {
+        "ms_per_step": ms, "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s",
+        "slices_per_s": nslices / (ms * 1e-3), "tensors": len(items), "slices": nslices,
+        "input_bytes": in_bytes, "status": int(st), "jacobi_sweeps_mean": mean_sw,
+        "autotuned": choice,
+        "max_rel_err_tol_items": max(r for (sh, it), r in zip(items, rels) if it["mode"] == "tol"),
         "roofline": {"bound": "alu", "kernel": "jacobi", "unit": "TFLOP/s", "peak": fp32_peak,
-                     "kernel_ms": choice["jacobi_ms"],
+                     "peak_source": fp32_src, "kernel_ms": choice["jacobi_ms"],
                      "algorithmic_flops": alg_flops,
                      "achieved": alg_flops / (choice["jacobi_ms"] * 1e-3) / 1e12},
         "clocks": clocks, "gpu_launches": N.tsvdm_batch_graph_kernels(b) * args.steps,
     }
-    line["roofline"]["frac"] = line["roofline"]["achieved"] / fp32_peak
+    out["roofline"]["frac"] = out["roofline"]["achieved"] / fp32_peak
     N.tsvdm_batch_destroy(b)
-    if args.fp64_compare:
+    if fp64_compare:
         b64, ios64, keep64 = make(N.F64, N.P_FP64)
         N.tsvdm_batch_run(b64, ios64)
         N.tsvdm_batch_capture(b64, ios64)
         ms64 = timed(b64, 1, 0)
-        line["fp64_gpu_ms_per_step"] = ms64
-        line["speedup_vs_fp64_gpu"] = ms64 / ms
+        rels64 = [float(k[7].item()) for k in keep64]
+        out["fp64_gpu"] = {"ms_per_step": ms64, "speedup_of_fp32_batch": ms64 / ms,
+                           "max_abs_rel_err_diff": max(abs(a - c) for a, c in zip(rels, rels64))}
         N.tsvdm_batch_destroy(b64)
+        del keep64
+    del keep
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch_bench(args, world, rank, local):
+    """The batch workload as the benchmark's line (input GB/s of one graph replay)."""
+    count = 64 if args.workload == "batch" else 8
+    b = batch_measure(args, local, count, args.fp64_compare)
+    line = {
+        "metric": METRIC, "value": b["value"], "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "slices_per_s": b["slices_per_s"], "ttm_precision": args.prec,
+        "config": {"workload": WORKLOADS[args.workload][2], "tensors": b["tensors"],
+                   "slices": b["slices"], "input_bytes": b["input_bytes"], "status": b["status"],
+                   "jacobi_sweeps_mean": b["jacobi_sweeps_mean"], "autotuned": b["autotuned"],
+                   "max_rel_err_tol_items": b["max_rel_err_tol_items"]},
+        "roofline": b["roofline"], "clocks": b["clocks"], "gpu_launches": b["gpu_launches"],
+    }
+    if "fp64_gpu" in b:
+        line["fp64_gpu_ms_per_step"] = b["fp64_gpu"]["ms_per_step"]
+        line["speedup_vs_fp64_gpu"] = b["fp64_gpu"]["speedup_of_fp32_batch"]
     print(json.dumps(line), flush=True)
 
 
@@ -348,7 +408,8 @@ def run_reference(args, wl):
     oracle.build_oracle()
     for _ in range(max(0, args.warmup)):
         A = oracle.ttm3(X, M, which=[0])
-    times = [cpu_sample(X, M, ns, cores) for _ in range(args.steps)]
+    which = spread(n3, ns)
+    times = [cpu_sample(X, M, which, cores)[0] for _ in range(args.steps)]
     t = statistics.mean(times)
     bytes_per_slice = n1 * n2 * 4
     gbs = ns * bytes_per_slice / t / 1e9
@@ -358,12 +419,199 @@ def run_reference(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "slices_per_s": ns / t,
         "config": {"workload": desc, "sample": "TTM + one-sided Jacobi SVD of %d of the %d "
-                   "slices per step" % (ns, n3)},
+                   "slices per step (spread over the spectrum)" % (ns, n3)},
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                          "sample": "%d slices of %dx%d per step" % (ns, n1, n2)},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def matched_error(plan, X, M, ranks, which, S_o, r):
+    """The north star's "matched" test on the oracle's sample: over the sampled slices, the
+    relative truncation error at the GPU's ranks from the GPU's singular values against the
+    same from the oracle's (FP64 TTM + Jacobi SVD of each slice), within 1e-5."""
+    import numpy as np
+    from paper_2605_16058_gb300 import native
+    full = plan.fixed_rank(X, M, r, rel_err=False)
+    S_g = full["S"].double().cpu().numpy().T          # r x n3
+    rk = ranks.cpu().numpy()
+    dg = tg = do = to = 0.0
+    for q, i in enumerate(which):
+        dg += float(np.sum(S_g[rk[i]:, i] ** 2))
+        tg += float(np.sum(S_g[:, i] ** 2))
+        do += float(np.sum(S_o[rk[i]:, q] ** 2))
+        to += float(np.sum(S_o[:, q] ** 2))
+    eg, eo = float(np.sqrt(dg / tg)), float(np.sqrt(do / to))
+    smax = float(S_g.max())
+    return {"sample_slices": len(which), "rel_err_gpu": eg, "rel_err_oracle": eo,
+            "abs_diff": abs(eg - eo), "tol": 1e-5, "matched": abs(eg - eo) <= 1e-5,
+            "max_sigma_err_over_sigma_max": float(max(
+                np.max(np.abs(S_g[:, i] - S_o[:, q])) for q, i in enumerate(which)) / smax)}
+
+
+def fp64_climate(Xh, Mh, shape, eps, ms_mixed, rel_mixed, stream):
+    """The all-FP64 GPU path (FP64 TTM, FP64 Jacobi, FP64 selection) on the same climate
+    input: one timed call (several seconds), against the mixed-precision step."""
+    import torch
+    from paper_2605_16058_gb300 import native
+    from paper_2605_16058_gb300.tsvdm import Plan
+    n1, n2, n3 = shape
+    r = min(n1, n2)
+    X = Xh.double().cuda()
+    M = Mh.double().cuda()
+    plan = Plan(n1, n2, n3, dtype=torch.float64, orthogonal=True, stream=stream)
+    cap = n3 * r
+    ranks = torch.empty(n3, dtype=torch.int32, device="cuda")
+    offs = torch.empty(n3 + 1, dtype=torch.int64, device="cuda")
+    U = torch.empty(cap, n1, dtype=torch.float64, device="cuda")
+    S = torch.empty(cap, dtype=torch.float64, device="cuda")
+    V = torch.empty(cap, n2, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tot, rel, st = native.tsvdm_tolerance(plan.handle, X, M, eps, ranks, offs, U, S, V, cap)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sweeps, _ = native.tsvdm_plan_stats(plan.handle)
+    plan.close()
+    del X, M, U, S, V
+    torch.cuda.empty_cache()
+    return {"ms_per_step": ms, "value": n1 * n2 * n3 * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s",
+            "input": "the same FP32 climate tensor, cast to FP64", "rel_err": rel,
+            "total_rank": int(tot), "status": int(st), "jacobi_sweeps_mean": sweeps / n3,
+            "speedup_of_mixed": ms / ms_mixed, "rel_err_diff_vs_mixed": abs(rel - rel_mixed),
+            "timing": "one call (CUDA events), after the mixed-precision runs"}
+
+
+def cfd_measure(args, stream):
+    """CFD-shaped 2048 x 256 x 512 FP32, DCT-II, t-SVDM-I k = 32, with the BF16x3 and TF32
+    tensor-core TTMs (FP32 Jacobi), against the all-FP64 GPU run on the same data and the
+    FP64 oracle on sampled slices: time, TTM roofline, error per output."""
+    import numpy as np
+    import torch
+    from paper_2605_16058_gb300 import native, synth
+    from paper_2605_16058_gb300.tsvdm import Plan
+    n1, n2, n3, k = 2048, 256, 512, 32
+    P = n1 * n2
+    Xn = synth.cfd(shape=(n1, n2, n3), seed=3)
+    Mn = synth.dct2_matrix(n3).astype(np.float32)
+    X = torch.from_numpy(np.ascontiguousarray(Xn.transpose(2, 1, 0))).cuda()
+    M = torch.from_numpy(np.ascontiguousarray(Mn.T)).cuda()
+    cores = os.cpu_count() or 1
+    which = spread(n3, cores)
+    t_o, U_o, S_o = cpu_sample(Xn, Mn.astype(np.float64), which, cores)
+    pk, src = peaks()
+    pr = probe_peaks()
+    out = {"workload": "CFD-shaped 2048x256x512 FP32 (40 travelling waves, 1e-4 noise), "
+                       "DCT-II, t-SVDM-I k=32", "oracle_sample_slices": len(which)}
+    res = {}
+    for prec in ("bf16x3", "tf32", "fp64"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        Xp, Mp = (X.double(), M.double()) if prec == "fp64" else (X, M)
+        plan = Plan(n1, n2, n3, dtype=dt, prec=prec, orthogonal=True, stream=stream)
+        U = torch.empty(n3, k, n1, dtype=dt, device="cuda")
+        S = torch.empty(n3, k, dtype=dt, device="cuda")
+        V = torch.empty(n3, k, n2, dtype=dt, device="cuda")
+        steps, warm = (1, 0) if prec == "fp64" else (args.steps, max(3, args.warmup))
+        for _ in range(warm):
+            native.tsvdm_fixed_rank(plan.handle, Xp, Mp, k, U, S, V, 0, True)
+        native.tsvdm_plan_profile(plan.handle, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stage = []
+        e0.record(stream)
+        for _ in range(steps):
+            rel, st = native.tsvdm_fixed_rank(plan.handle, Xp, Mp, k, U, S, V, 0, True)
+            stage.append(native.tsvdm_plan_profile_read(plan.handle)[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ttm_ms = statistics.mean(s_["ttm"] for s_ in stage)
+        jac_ms = statistics.mean(s_["jacobi"] for s_ in stage)
+        d = {"ms_per_step": ms, "value": P * n3 * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s",
+             "slices_per_s": n3 / (ms * 1e-3), "rel_err": rel, "status": int(st),
+             "ttm_ms": ttm_ms, "jacobi_ms": jac_ms, "steps": steps}
+        byts = (2 * P * n3 + n3 * n3) * (8 if prec == "fp64" else 4)
+        d["ttm_hbm"] = {"achieved": byts / (ttm_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                        "unit": "GB/s", "frac": byts / (ttm_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                        "peak_source": "of " + src}
+        if prec != "fp64":
+            terms = 3 if prec == "bf16x3" else 1
+            flops = terms * 2.0 * P * n3 * n3
+            peak = pr["bf16_mma"] if prec == "bf16x3" else pr["tf32_mma"]
+            d["ttm_tensor"] = {"achieved": flops / (ttm_ms * 1e-3) / 1e12, "peak": peak,
+                               "unit": "TFLOP/s", "frac": flops / (ttm_ms * 1e-3) / 1e12 / peak,
+                               "flops": flops, "peak_source": "measured on this GPU (%s MMA "
+                               "probe)" % ("BF16" if prec == "bf16x3" else "TF32"),
+                               "note": "BF16x3 counts its three BF16 products"}
+        Sg = S.double().cpu().numpy().T           # k x n3
+        Ug = U.double().cpu().numpy().transpose(2, 1, 0)   # n1 x k x n3
+        smax = float(Sg.max())
+        sig_err = max(float(np.max(np.abs(Sg[:, i] - S_o[:k, q]))) for q, i in enumerate(which))
+        pd, npd = 0.0, 0
+        for q, i in enumerate(which):
+            if S_o[k - 1, q] - S_o[k, q] > 1e-2 * smax:
+                a, b = U_o[:, :k, q], Ug[:, :, i]
+                pd = max(pd, float(np.linalg.norm(a @ a.T - b @ b.T)))
+                npd += 1
+        d["vs_oracle"] = {"sigma_max_abs_err_over_sigma_max": sig_err / smax,
+                          "U_projector_max_diff": pd if npd else None,
+                          "U_projector_slices": npd,
+                          "note": "projectors of the rank-k subspace where the gap at k "
+                                  "exceeds 1e-2 sigma_max"}
+        res[prec] = (d, Sg)
+        plan.close()
+        del U, S, V
+        torch.cuda.empty_cache()
+    S64 = res["fp64"][1]
+    for prec in ("bf16x3", "tf32", "fp64"):
+        d, Sg = res[prec]
+        if prec != "fp64":
+            d["vs_fp64_gpu"] = {"rel_err_diff": abs(d["rel_err"] - res["fp64"][0]["rel_err"]),
+                                "sigma_max_abs_err_over_sigma_max":
+                                    float(np.max(np.abs(Sg - S64)) / S64.max()),
+                                "speedup": res["fp64"][0]["ms_per_step"] / d["ms_per_step"]}
+        out[prec] = d
+    return out
+
+
+def config0_measure():
+    """The 64 x 48 x 16 FP64 t-SVDM-I case (k = 8, DCT-II): GPU call time (median of 20
+    after 3 warm-ups) and error, the oracle single-threaded beside it."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2605_16058_gb300 import synth
+    from paper_2605_16058_gb300.tsvdm import Plan
+    c = synth.smoke_case()
+    Xn, Mn, k = c["X"], c["M"], c["k"]
+    n1, n2, n3 = Xn.shape
+    X = torch.from_numpy(np.ascontiguousarray(Xn.transpose(2, 1, 0))).cuda()
+    M = torch.from_numpy(np.ascontiguousarray(np.asarray(Mn).T)).cuda()
+    plan = Plan(n1, n2, n3, dtype=torch.float64)
+    for _ in range(3):
+        out = plan.fixed_rank(X, M, k)
+    ts = []
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = plan.fixed_rank(X, M, k)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    plan.close()
+    to = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        ref = oracle.fixed_rank(Xn, Mn, k, threads=1)
+        to.append((time.perf_counter() - t0) * 1e3)
+    return {"workload": "64x48x16 FP64 CP tensor (12 terms), DCT-II, t-SVDM-I k=8",
+            "gpu_ms": statistics.median(ts), "rel_err_gpu": out["rel_err"],
+            "oracle_ms_single_thread": statistics.median(to), "rel_err_oracle": ref["rel_err"],
+            "rel_err_diff": abs(out["rel_err"] - ref["rel_err"]),
+            "timing": "GPU: CUDA events around the call (it synchronises for rel_err)"}
 
 
 def main():
@@ -394,6 +642,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    probes = probe_peaks()
 
     shape, eps, desc = wl
     n1, n2 = shape[0], shape[1]
@@ -406,6 +655,8 @@ def main():
         Mh = torch.from_numpy(np.ascontiguousarray(Mn.T.astype(np.float32))).pin_memory()
         plan = Plan(n1, n2, n3, dtype=torch.float32, prec=args.prec, orthogonal=True,
                     stream=stream)
+        plan.set_angle_precision(args.angles)
+        plan.set_vectors(args.vectors)
         msizes = [n3]
     else:
         # one DCT-II per trailing mode, concatenated; the CPU baseline uses the equivalent
@@ -455,6 +706,7 @@ def main():
         dist.barrier()
     clocks = clk.stop()
     ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    ranks_timed = ranks.clone()
     sweeps, rots = native.tsvdm_plan_stats(plan.handle)
     native.tsvdm_plan_profile(plan.handle, 0)
     in_bytes = n1 * n2 * n3 * 4
@@ -527,7 +779,7 @@ def main():
     m_, p_ = max(n1, n2), min(n1, n2)
     alg_flops = sweeps * 3.0 * m_ * p_ * (p_ - 1) + rots * 6.0 * (m_ + p_)
     pk, src = peaks()
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak, fp32_src = fp32_peak_tflops()
     achieved = alg_flops / (jac_ms * 1e-3) / 1e12
     ttm_ms = statistics.mean(s["ttm"] for s in stage_ms)
     # one read and one write of the tensor per transformed mode (plus each matrix)
@@ -549,7 +801,7 @@ def main():
                      "traffic": (None if jacobi_traffic_per_slice() is None
                                  else jacobi_traffic_per_slice() * n3),
                      "traffic_note": "ncu dram bytes per slice (1024x512x304 capture) x slices",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "peak_source": fp32_src,
                      "note": "classical one-sided Jacobi flop count (3 m p (p-1) per sweep + "
                              "6 (m + p) per rotation) against the FP32 CUDA-core peak; the "
                              "Gram and rotation apply run as split products on tcgen05, the "
@@ -593,14 +845,27 @@ def main():
                              "fwd_bwd_ms_per_step": ms_w, "loss_first": lw[0],
                              "loss_last": lw[-1], "cold_start_ms_per_step": ms_c,
                              "cold_start_loss_last": lc[-1]}
+    line["peaks_measured"] = dict(
+        {k + "_tflops": v for k, v in probes.items()},
+        how="tsvdm_probe_peak: FP32/FP64 FMA loops (8 chains per thread, full occupancy) and "
+            "tcgen05 kind::tf32 / kind::f16 M=128 N=256 MMA loops (one CTA per SM); best of 3")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        ns = min(cores, n3)
-        tcpu = cpu_sample(Xn, Mn, ns, cores)
+        which = spread(n3, cores)
+        ns = len(which)
+        tcpu, U_o, S_o = cpu_sample(Xn, Mn, which, cores)
         cgbs = ns * n1 * n2 * 4 / tcpu / 1e9
         line["cpu_baseline"] = {"value": cgbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                                 "sample": "FP64 TTM + one-sided Jacobi SVD of %d of the %d "
-                                          "slices (%.1f s)" % (ns, n3, tcpu)}
+                                          "slices spread over the spectrum (%.1f s)"
+                                          % (ns, n3, tcpu)}
+        if len(shape) == 3:
+            line["matched"] = matched_error(plan, X, M, ranks_timed, which, S_o, r)
+    if rank == 0 and world == 1 and not args.quick and len(shape) == 3:
+        line["fp64_gpu"] = fp64_climate(Xh, Mh, (n1, n2, n3), eps, ms_step, rel, stream)
+        line["cfd"] = cfd_measure(args, stream)
+        line["batch"] = batch_measure(args, local, 64, True)
+        line["config0"] = config0_measure()
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -63,8 +63,9 @@ typedef enum {
 typedef enum { TSVDM_F32 = 0, TSVDM_F64 = 1 } tsvdm_dtype;
 
 /* Arithmetic of the mode-3 TTMs.  The slice SVDs run in the storage precision (FP32
- * data, angles and convergence test for F32; FP64 for F64); see tsvdm_plan_set_engine
- * for the engine of their dense products.
+ * data and rotations for F32, with the rotation angle and the convergence test in FP64;
+ * FP64 for F64); see tsvdm_plan_set_engine for the engine of their dense products and
+ * tsvdm_plan_set_angle_precision for the angle arithmetic.
  *   TSVDM_P_FP64    FP64 CUDA-core products (dtype F64 only)
  *   TSVDM_P_FP32    FP32 CUDA-core products (dtype F32)
  *   TSVDM_P_TF32    one TF32 tensor-core product, FP32 accumulation (dtype F32)
@@ -178,6 +179,48 @@ typedef enum {
 } tsvdm_jacobi_engine;
 tsvdm_status tsvdm_plan_set_engine(tsvdm_plan plan, int engine);
 
+/* Arithmetic of the rotation test and angle of the slice SVDs for F32 plans (the scalar
+ * method's zeta = (b - a) / (2 g), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+ * c = 1 / sqrt(1 + t^2), s = c t, and the test |g| > tol sqrt(a b), on the FP32 Gram
+ * entries a = ||w_i||^2, b = ||w_j||^2, g = w_i^T w_j; Sec. 3.2's per-slice svd):
+ *   TSVDM_ANGLE_FP64  (default) the test is decided and t, c, s and the rotated diagonal
+ *                     are computed in FP64, then rounded to FP32 for the rotation;
+ *   TSVDM_ANGLE_FP32  both in FP32 (opt-in: cheaper on GPUs whose FP64 rate is low; the
+ *                     rotation is applied to freshly formed Grams, so the angle's rounding
+ *                     moves the convergence rate, not the accuracy of the columns).
+ * F64 plans always use FP64.  EINVAL for other values. */
+typedef enum { TSVDM_ANGLE_FP64 = 0, TSVDM_ANGLE_FP32 = 1 } tsvdm_angle_prec;
+tsvdm_status tsvdm_plan_set_angle_precision(tsvdm_plan plan, int angles);
+
+/* How the singular vectors are formed (Sec. 3.4's strategies for t-SVDM-II; the same two
+ * forms serve t-SVDM-I):
+ *   TSVDM_VECTORS_ACCUMULATE   (default; the "truncate" strategy) one pass: every slice's
+ *                              Jacobi accumulates its rotations into V, the kept triplets
+ *                              are taken from the full decomposition;
+ *   TSVDM_VECTORS_SECOND_PASS  two passes (the compute-efficient strategy): the Jacobi runs
+ *                              without right vectors (the slices' singular values, and the
+ *                              work matrix W = A V whose normalised columns are one side of
+ *                              each triplet); the ranks are chosen; then only the kept
+ *                              triplets' other side is formed from the slice itself,
+ *                              v_j = A^T u_j / sigma_j (u_j = A v_j / sigma_j for n1 < n2;
+ *                              0 where sigma_j = 0), in the plan's precision.  Its rounding
+ *                              error is about u ||A|| / sigma_j per vector, the order of the
+ *                              rank-k subspace error of the one-pass form (u ||A|| / gap).
+ * A warm-started decomposition (tsvdm_plan_set_warm_start) always uses the one-pass form.
+ * The first SECOND_PASS on a plan with n1 >= n2 allocates n1 n2 n3 elements (a copy of the
+ * transformed slices that the Jacobi works on, so that the second pass reads the slices
+ * themselves); ENOMEM if that fails.  EINVAL for other values. */
+typedef enum { TSVDM_VECTORS_ACCUMULATE = 0, TSVDM_VECTORS_SECOND_PASS = 1 } tsvdm_vectors;
+tsvdm_status tsvdm_plan_set_vectors(tsvdm_plan plan, int mode);
+
+/* Bound of the waits of the tensor-core slice-SVD kernel's scheduler (a worker waiting for
+ * the two column blocks of its block pair, or for work to appear): after `polls` polls
+ * (about a microsecond each) the kernel stops every worker and the call reports
+ * TSVDM_ETIMEOUT (tsvdm_last_status; the outputs are then undefined).  0 restores the
+ * default (2^24 polls, several seconds).  The plan stays usable after a timeout.  EINVAL for
+ * polls < 0 or above 2^32 - 1. */
+tsvdm_status tsvdm_plan_set_wait_limit(tsvdm_plan plan, int64_t polls);
+
 /* Y = X x_3 M (inverse = 0) or Y = X x_3 M^{-1} (inverse = 1), Sec. 2.1.  For
  * inverse = 1 on an orthogonal plan, M is the forward matrix and M^T / c^2 is applied;
  * on a non-orthogonal plan, M must already hold M^{-1}.  X, Y: n1 x n2 x n3 device,
@@ -224,7 +267,9 @@ tsvdm_status tsvdm_tolerance(tsvdm_plan plan, const void *X, const void *M, doub
 
 /* Packs the factors kept by the most recent tsvdm_tolerance call on this plan into
  * device buffers U (n1 x capacity), S (capacity), V (n2 x capacity).  ECAPACITY if
- * capacity is below that call's total rank; EINVAL if no tolerance call preceded. */
+ * capacity is below that call's total rank; EINVAL if no tolerance call preceded.  With
+ * TSVDM_VECTORS_SECOND_PASS the second pass runs here, and only one pack follows each
+ * tsvdm_tolerance call (a second one returns EINVAL). */
 tsvdm_status tsvdm_tolerance_pack(tsvdm_plan plan, void *U, void *S, void *V,
                                   int64_t capacity);
 
@@ -279,6 +324,25 @@ typedef enum {
 } tsvdm_stage;
 tsvdm_status tsvdm_plan_profile(tsvdm_plan plan, int enable);
 tsvdm_status tsvdm_plan_profile_read(tsvdm_plan plan, float *ms, int64_t *launches);
+
+/* Measured peak rates for roofline fractions (instrumentation; the paper has no
+ * counterpart).  Runs one warm-up and one timed launch of a kernel that does nothing but the
+ * unit's instruction on every SM, and returns the rate in TFLOP/s (synchronises; allocates
+ * and frees a 4-byte status word):
+ *   TSVDM_PROBE_FP32_FMA  FP32 FMA on the CUDA cores (256-thread CTAs, full occupancy,
+ *                         8 independent chains per thread), iters FMAs per chain
+ *   TSVDM_PROBE_TF32_MMA  tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, one CTA per SM,
+ *                         iters MMAs per SM, operands in shared memory
+ *   TSVDM_PROBE_BF16_MMA  the same with kind::f16 (BF16, K = 16)
+ *   TSVDM_PROBE_FP64_FMA  FP64 FMA on the CUDA cores, as the FP32 probe
+ * EINVAL for another unit or iters < 1; ETIMEOUT if the MMA completion wait ran out. */
+typedef enum {
+  TSVDM_PROBE_FP32_FMA = 0,
+  TSVDM_PROBE_TF32_MMA = 1,
+  TSVDM_PROBE_BF16_MMA = 2,
+  TSVDM_PROBE_FP64_FMA = 3
+} tsvdm_probe_unit;
+tsvdm_status tsvdm_probe_peak(int unit, int64_t iters, void *stream, double *tflops);
 
 /* ---- learned orthogonal transform (extension) -------------------------------------
  * Cayley form M(A) = (I + W)^{-1} (I - W) M0 with W = A^T - A skew-symmetric.
@@ -353,21 +417,25 @@ tsvdm_status tsvdm_batch_graph_kernels(tsvdm_batch b, int64_t *kernels);
  * callers that must not call cudaMalloc (a process whose device memory is all handed to
  * another allocator up front, or a service that forbids allocation on its request path
  * because a driver allocation can synchronise the device and take milliseconds).
- * Same computation as the selection inside tsvdm_tolerance: Algorithm 2 steps 2-8 on
- * given singular values, with its scratch in a fixed 2 MiB array built into the
- * library (held on every GPU that loads it until the process exits) instead of a plan.
+ * It is the same computation as the selection inside tsvdm_tolerance, on given singular
+ * values, with its scratch in a fixed array of about 2.1 MiB built into the library (held
+ * on every GPU that loads it until the process exits) instead of a plan.
  *   sigma    device float [cols x nslices], column i = slice i's singular values sorted
- *            in descending order (e.g. S of tsvdm_fixed_rank with k = min(n1, n2))
+ *            in descending order (e.g. S of tsvdm_fixed_rank with k = min(n1, n2)); they
+ *            must be finite and non-negative (-0 counts as 0)
  *   eps      relative tolerance in (0, 1)
  *   ranks    device int32 [nslices]; offsets device int64 [nslices + 1] (as tsvdm_tolerance)
  *   summary  device double [4] or NULL: sum of all sigma^2, sum of discarded sigma^2,
  *            tau (a sigma^2 value, -1 when nothing is discarded), total rank
  *   stream   cudaStream_t
  * At most 262,144 singular values per call (cols * nslices); larger problems return
- * TSVDM_ESCRATCH without launching anything.  Nothing is allocated.  The first call on a
- * device looks up the scratch's device address (once per device, with that device
- * current); make that first call before any stream capture.  Every call shares the
- * scratch, so calls whose work overlaps on the GPU race: issue them on one stream. */
+ * TSVDM_ESCRATCH without launching anything.  Nothing is allocated.  The call is
+ * asynchronous: a NaN, infinite or negative value is reported on the device, as NaN in all
+ * four summary entries with every rank and offset 0.  Each call looks up the scratch's
+ * device address on the current device (a host-side lookup; the first one on a device may
+ * load the library's device code, so make the first call before any stream capture).
+ * Every call shares the scratch and clears what must start at zero itself, so calls whose
+ * work overlaps on the GPU race: issue them on one stream. */
 tsvdm_status tsvdm_select_ranks_noalloc(const float *sigma, int64_t cols, int64_t nslices,
                                         double eps, int32_t *ranks, int64_t *offsets,
                                         double *summary, void *stream);

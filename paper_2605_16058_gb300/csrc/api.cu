@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -40,6 +41,20 @@ struct tsvdm_plan_s {
   int max_sweeps = 40;
   int width_hint = 0, cluster_hint = 0, grid_hint = 0, stages_hint = 0, inner_sweeps = 2;
   int engine = JACOBI_AUTO;
+  int angle32 = 0;           // FP32 slices: rotation test and angle in FP32 (opt-in)
+  long long wait_polls = 0;  // bound of the tensor-core Jacobi's scheduler waits (0: default)
+  int vec_mode = 0;          // TSVDM_VECTORS_ACCUMULATE / TSVDM_VECTORS_SECOND_PASS
+  int twopass = 0;           // the last decomposition ran without right vectors
+  // second pass: one restricted-Jacobi entry per slice with kept columns (device arrays of
+  // n3 entries, their host images, and the restricted Jacobi's sweep counts)
+  SliceDesc *tp_desc = nullptr;
+  int64_t *tp_off = nullptr;
+  int *tp_sweeps = nullptr;
+  void *tp_sig = nullptr;    // the restricted Jacobi's singular values and order (cols n3)
+  int *tp_perm = nullptr;
+  std::vector<SliceDesc> tp_hdesc;
+  std::vector<int64_t> tp_hoff;
+  std::vector<int> tp_hranks;
   // d-way tensors: the trailing modes (dims td[0..dw-1], n3 = their product), one matrix
   // per mode, concatenated in the M buffer at element offsets mo[]; dw = 0: 3-way plan
   int dw = 0;
@@ -93,7 +108,11 @@ double default_tol(const tsvdm_plan_s *p) {
   return 4.0 * sqrt((double)p->rows) * u;
 }
 
-void *work_matrix(tsvdm_plan_s *p) { return p->transposed ? p->Wt : p->Ahat; }
+// The Jacobi's matrix: the transposed copy, or (a decomposition without right vectors on a
+// non-transposed plan) a copy of Ahat, which the second pass then reads; else Ahat itself.
+void *work_matrix(tsvdm_plan_s *p) {
+  return (p->transposed || p->twopass) ? p->Wt : p->Ahat;
+}
 
 // Start of a call: forget the previous call's stage record.
 void begin_call(tsvdm_plan_s *p) {
@@ -241,10 +260,18 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   const int64_t P = p->n1 * p->n2;
   tsvdm_status s = run_ttm<T>(p, X, P, M, false, (T *)p->Ahat, nullptr);
   if (s != TSVDM_OK) return s;
+  // two passes (Sec. 3.4): singular values first, the kept vectors afterwards; a warm start
+  // needs the right vectors, so it keeps the one-pass form
+  p->twopass = (p->vec_mode == TSVDM_VECTORS_SECOND_PASS && !p->warm) ? 1 : 0;
   if (p->transposed) {
     stage_begin(p, TSVDM_STAGE_TRANSPOSE);
     CK(transpose_slices<T>((const T *)p->Ahat, p->n1, p->n2, p->n3, (T *)p->Wt, p->st));
     stage_end(p, TSVDM_STAGE_TRANSPOSE, 1);
+  } else if (p->twopass) {
+    stage_begin(p, TSVDM_STAGE_TRANSPOSE);
+    CK(cudaMemcpyAsync(p->Wt, p->Ahat, p->esz * p->n1 * p->n2 * p->n3, cudaMemcpyDeviceToDevice,
+                       p->st));
+    stage_end(p, TSVDM_STAGE_TRANSPOSE, 0);
   }
   CK(cudaMemsetAsync(p->queue, 0, sizeof(int), p->st));
   CK(cudaMemsetAsync(p->rots, 0, sizeof(long long) * p->n3, p->st));
@@ -278,6 +305,9 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   jp.desc = nullptr;
   jp.engine = p->engine;
   jp.warm = warm ? 1 : 0;
+  jp.angle32 = p->angle32;
+  jp.wait_polls = p->wait_polls;
+  jp.novec = p->twopass;
   jp.sched = p->sched;
   jp.sched_bytes = p->sched_bytes;
   jp.max_cols = (int)p->cols;
@@ -292,15 +322,103 @@ tsvdm_status decompose(tsvdm_plan_s *p, const T *X, const T *M) {
   return TSVDM_OK;
 }
 
+// Second pass of a decomposition without right vectors (Sec. 3.4), after the emitted side
+// K (U, or V for transposed slices) and S: Z = A^T K (A K) into the other side's buffer O,
+// a restricted one-sided Jacobi of every slice's Z (its kept columns only), then O = the
+// normalised columns of Z R, K <- K R, S = their norms (descending), and the sign rule.
+// Ahat and the work matrix are free by then and hold the rotated copies.
+template <typename T>
+tsvdm_status second_pass(tsvdm_plan_s *p, int64_t k, const int *ranks, const int64_t *offsets,
+                         T *U, T *S, T *V, int *nl) {
+  const bool tr = p->transposed != 0;
+  const int64_t kd = p->rows, od = p->cols, n3 = p->n3;
+  T *Kout = tr ? V : U, *Oout = tr ? U : V;
+  const int64_t maxr = ranks ? p->cols : k;
+  CK(complete_vectors<T>((const T *)p->Ahat, p->n1, p->n2, n3, tr, k, ranks, offsets, maxr, U,
+                         nullptr, V, p->st));
+  // the kept columns of every slice (ranks are read back: the descriptors are built here)
+  p->tp_hranks.assign(n3, (int)k);
+  if (ranks) {
+    CK(cudaMemcpyAsync(p->tp_hranks.data(), ranks, sizeof(int) * n3, cudaMemcpyDeviceToHost,
+                       p->st));
+    CK(cudaStreamSynchronize(p->st));
+  }
+  p->tp_hdesc.clear();
+  p->tp_hoff.clear();
+  int64_t col = 0, roff = 0;
+  int max_rho = 0, min_rho = 1 << 30;
+  for (int64_t i = 0; i < n3; ++i) {
+    const int rho = p->tp_hranks[i];
+    if (rho >= 1) {
+      SliceDesc d;
+      d.A = Oout + col * od;
+      d.V = (T *)p->Vw + roff;
+      d.norm2 = p->norm2 + col;
+      d.sig = (T *)p->tp_sig + col;
+      d.perm = p->tp_perm + col;
+      d.rows = (int)od;
+      d.cols = rho;
+      p->tp_hdesc.push_back(d);
+      p->tp_hoff.push_back(col);
+      max_rho = rho > max_rho ? rho : max_rho;
+      min_rho = rho < min_rho ? rho : min_rho;
+    }
+    col += rho;
+    roff += (int64_t)rho * rho;
+  }
+  const int count = (int)p->tp_hdesc.size();
+  if (count == 0) return TSVDM_OK;
+  const int64_t total = col;
+  CK(cudaMemcpyAsync(p->tp_desc, p->tp_hdesc.data(), sizeof(SliceDesc) * count,
+                     cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(p->tp_off, p->tp_hoff.data(), sizeof(int64_t) * count,
+                     cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemsetAsync(p->queue, 0, sizeof(int), p->st));
+  JacobiParams jp{};
+  jp.rows = 0;
+  jp.cols = min_rho;
+  jp.nslices = count;
+  jp.tol = p->tol > 0 ? p->tol
+                      : 4.0 * sqrt((double)od) * (sizeof(T) == 4 ? ldexp(1.0, -24) : ldexp(1.0, -53));
+  jp.max_sweeps = p->max_sweeps;
+  jp.queue = p->queue;
+  jp.status = p->status;
+  jp.sweeps = p->tp_sweeps;
+  jp.rots = p->rots;
+  jp.norm2 = nullptr;
+  jp.inner_sweeps = p->inner_sweeps;
+  jp.desc = p->tp_desc;
+  jp.engine = (sizeof(T) == 4 && p->engine != JACOBI_FMA) ? JACOBI_TC : JACOBI_FMA;
+  jp.sched = p->sched;
+  jp.sched_bytes = p->sched_bytes;
+  jp.max_cols = max_rho;
+  jp.angle32 = p->angle32;
+  jp.wait_polls = p->wait_polls;
+  CK(jacobi_run<T>(jp, p->st, 0, 0, 0, 0));
+  CK(jacobi_finalize_desc<T>(p->tp_desc, count, max_rho, p->st));
+  T *Ktmp = (T *)p->Ahat, *Otmp = (T *)p->Wt;
+  CK(rotate_back<T>(p->tp_desc, p->tp_off, count, max_rho, kd, od, Kout, Ktmp, Otmp, S, p->st));
+  CK(cudaMemcpyAsync(Kout, Ktmp, sizeof(T) * kd * total, cudaMemcpyDeviceToDevice, p->st));
+  CK(cudaMemcpyAsync(Oout, Otmp, sizeof(T) * od * total, cudaMemcpyDeviceToDevice, p->st));
+  CK(emit_signfix<T>(p->n1, p->n2, n3, k, ranks, offsets, maxr, U, V, p->st));
+  *nl += 5;
+  return TSVDM_OK;
+}
+
 template <typename T>
 tsvdm_status emit(tsvdm_plan_s *p, int64_t k, const int *ranks, const int64_t *offsets, T *U,
                   T *S, T *V) {
   stage_begin(p, TSVDM_STAGE_EMIT);
-  CK(emit_factors<T>((const T *)work_matrix(p), p->rows * p->cols, (const T *)p->Vw,
-                     p->cols * p->cols, (int)p->rows, (int)p->cols, (int)p->n3,
-                     p->transposed != 0, (const T *)p->sig, p->perm, k, ranks, offsets, U, S, V,
-                     p->st));
-  stage_end(p, TSVDM_STAGE_EMIT, 1);
+  CK(emit_factors<T>((const T *)work_matrix(p), p->rows * p->cols,
+                     p->twopass ? nullptr : (const T *)p->Vw, p->cols * p->cols, (int)p->rows,
+                     (int)p->cols, (int)p->n3, p->transposed != 0, (const T *)p->sig, p->perm, k,
+                     ranks, offsets, U, S, V, p->st));
+  int nl = 1;
+  if (p->twopass) {
+    tsvdm_status s = second_pass<T>(p, k, ranks, offsets, U, S, V, &nl);
+    if (s != TSVDM_OK) return s;
+  }
+  stage_end(p, TSVDM_STAGE_EMIT, nl);
   return TSVDM_OK;
 }
 
@@ -363,8 +481,8 @@ tsvdm_status tolerance_impl(tsvdm_plan_s *p, const void *X, const void *M, doubl
   if ((s = decompose<T>(p, (const T *)dX, (const T *)dM)) != TSVDM_OK) return s;
   stage_begin(p, TSVDM_STAGE_SELECT);
   CK(select_ranks<T>((const T *)p->sig, (int)p->cols, (int)n3, eps, p->keys, p->scal,
-                     p->ranks_ws, p->off_ws, p->st));
-  stage_end(p, TSVDM_STAGE_SELECT, 1);
+                     p->ranks_ws, p->off_ws, p->status, p->st));
+  stage_end(p, TSVDM_STAGE_SELECT, select_launches(sizeof(T) == 8));
   double sc[SC_COUNT];
   CK(cudaMemcpyAsync(sc, p->scal, sizeof(sc), cudaMemcpyDeviceToHost, p->st));
   if (ranks)
@@ -396,6 +514,7 @@ tsvdm_status pack_impl(tsvdm_plan_s *p, void *U, void *S, void *V) {
   if ((s = stage_in(p, STG_V, V, e * p->n2 * (tot > 0 ? tot : 1), false, &dV, &sV)) != TSVDM_OK) return s;
   if (tot > 0) {
     if ((s = emit<T>(p, 0, p->ranks_ws, p->off_ws, (T *)dU, (T *)dS, (T *)dV)) != TSVDM_OK) return s;
+    if (p->twopass) p->tol_valid = 0;   // the second pass used the kept slices as scratch
     if (sU) CK(cudaMemcpyAsync(U, dU, e * p->n1 * tot, cudaMemcpyDeviceToHost, p->st));
     if (sS) CK(cudaMemcpyAsync(S, dS, e * tot, cudaMemcpyDeviceToHost, p->st));
     if (sV) CK(cudaMemcpyAsync(V, dV, e * p->n2 * tot, cudaMemcpyDeviceToHost, p->st));
@@ -470,7 +589,8 @@ tsvdm_status backward_impl(tsvdm_plan_s *p, const void *X, const void *M, int64_
 bool valid_plan(tsvdm_plan p) { return p != nullptr && p->Ahat != nullptr; }
 
 void free_plan(tsvdm_plan_s *p) {
-  void *bufs[] = {p->Ahat, p->Wt, p->Vw, p->sig, p->keys, p->perm, p->sweeps, p->status,
+  void *bufs[] = {p->tp_desc, p->tp_off, p->tp_sweeps, p->tp_sig, p->tp_perm, p->Ahat, p->Wt, p->Vw, p->sig, p->keys,
+                  p->perm, p->sweeps, p->status,
                   p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk, p->tc_ws,
                   p->norm2, p->sched, p->dtmp, p->warm_buf};
   for (void *b : bufs)
@@ -503,6 +623,7 @@ tsvdm_status data_transform_impl(tsvdm_plan_s *p, const void *X, void *M) {
                           1, p->st, &sub);
     if (s != TSVDM_OK) return s;
     sub->engine = p->engine;
+    sub->angle32 = p->angle32;
     if (cudaMalloc(&p->dbuf, e * (3 * n * n + n + 16)) != cudaSuccess) {
       cudaGetLastError();
       free_plan(sub);
@@ -590,7 +711,7 @@ tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype d
   AL(p->Vw, e * nv);
   AL(p->sig, e * ns);
   AL(p->perm, sizeof(int) * ns);
-  AL(p->keys, 2 * sizeof(unsigned long long) * ns);
+  AL(p->keys, select_workspace_bytes(p->cols, n3));
   AL(p->sweeps, sizeof(int) * n3);
   AL(p->rots, sizeof(long long) * n3);
   AL(p->norm2, sizeof(float) * ns);
@@ -599,6 +720,9 @@ tsvdm_status tsvdm_plan_create(int64_t n1, int64_t n2, int64_t n3, tsvdm_dtype d
   p->sched_bytes = jacobi_sched_bytes(n3, p->cols);
   AL(p->sched, p->sched_bytes);
   AL(p->ranks_ws, sizeof(int) * n3);
+  AL(p->tp_desc, sizeof(SliceDesc) * n3);
+  AL(p->tp_off, sizeof(int64_t) * n3);
+  AL(p->tp_sweeps, sizeof(int) * n3);
   AL(p->off_ws, sizeof(int64_t) * (n3 + 1));
   AL(p->scal, sizeof(double) * SC_COUNT);
   AL(p->splitk, sizeof(double) * p->splitk_elems);
@@ -692,6 +816,38 @@ tsvdm_status tsvdm_plan_set_engine(tsvdm_plan plan, int engine) {
   if (engine == TSVDM_JACOBI_TC && plan->dtype != TSVDM_F32) return TSVDM_ENOTSUP;
   plan->engine = engine == TSVDM_JACOBI_TC ? JACOBI_TC
                                            : (engine == TSVDM_JACOBI_FMA ? JACOBI_FMA : JACOBI_AUTO);
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_set_angle_precision(tsvdm_plan plan, int angles) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  if (angles != TSVDM_ANGLE_FP64 && angles != TSVDM_ANGLE_FP32) return TSVDM_EINVAL;
+  plan->angle32 = angles == TSVDM_ANGLE_FP32 ? 1 : 0;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_set_vectors(tsvdm_plan plan, int mode) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  if (mode != TSVDM_VECTORS_ACCUMULATE && mode != TSVDM_VECTORS_SECOND_PASS) return TSVDM_EINVAL;
+  if (mode == TSVDM_VECTORS_SECOND_PASS) {
+    const size_t ns = (size_t)plan->cols * plan->n3;
+    cudaError_t e = cudaSuccess;
+    if (!plan->Wt) e = cudaMalloc(&plan->Wt, plan->esz * (size_t)plan->n1 * plan->n2 * plan->n3);
+    if (e == cudaSuccess && !plan->tp_sig) e = cudaMalloc(&plan->tp_sig, plan->esz * ns);
+    if (e == cudaSuccess && !plan->tp_perm) e = cudaMalloc((void **)&plan->tp_perm, sizeof(int) * ns);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return TSVDM_ENOMEM;
+    }
+  }
+  plan->vec_mode = mode;
+  plan->tol_valid = 0;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_set_wait_limit(tsvdm_plan plan, int64_t polls) {
+  if (!valid_plan(plan) || polls < 0 || polls > 0xffffffffLL) return TSVDM_EINVAL;
+  plan->wait_polls = polls;
   return TSVDM_OK;
 }
 

@@ -84,6 +84,10 @@ struct JacobiParams {
   size_t sched_bytes;  //   by jacobi_run before the launch
   int max_cols;        // largest cols of any slice (sizes the scheduler state)
   int warm;            // 1: V already holds the starting rotation (warm start), keep it
+  int angle32;         // FP32 slices: 1 = rotation test and angle in FP32, 0 = in FP64
+  long long wait_polls;  // polls of the tensor-core kernel's dependency and idle waits
+                         //   (0 = the default bound)
+  int novec;           // 1: no right vectors (V is neither initialised nor rotated)
 };
 enum { JACOBI_AUTO = 0, JACOBI_FMA = 1, JACOBI_TC = 2 };
 
@@ -102,17 +106,50 @@ template <typename T>
 cudaError_t jacobi_finalize_desc(const SliceDesc *desc, int nslices, int max_cols,
                                  cudaStream_t st);
 
-// Writes normalised, sign-fixed factors of slices (see emit in jacobi.cu).
+// Writes normalised, sign-fixed factors of slices (see emit in jacobi.cu).  Vw == nullptr
+// (a decomposition without right vectors): only the work matrix's side is written (U for
+// non-transposed slices, sign-fixed; V for transposed ones, sign left to emit_signfix) and
+// S; complete_vectors then forms the other side.
 template <typename T>
 cudaError_t emit_factors(const T *A, int64_t sA, const T *Vw, int64_t sV, int rows, int cols,
                          int nslices, bool transposed, const T *sig, const int *perm,
                          int64_t k_uniform, const int *ranks, const int64_t *offsets, T *U,
                          T *S, T *V, cudaStream_t st);
-
-// t-SVDM-II selection (Algorithm 2) on the sorted singular values sig (cols x nslices).
+// Second pass of a decomposition without right vectors: for every emitted column j of slice
+// i (uniform k, or packed ranks/offsets), the vector of the other side from the slice
+// Ahat_i (n1 x n2, column-major, slices n1 n2 apart) and the emitted one:
+//   non-transposed (n1 >= n2): V(:, j) = Ahat_i^T U(:, j) / S_j
+//   transposed     (n1 <  n2): U(:, j) = Ahat_i   V(:, j) / S_j    (0 where S_j = 0)
 template <typename T>
-cudaError_t select_ranks(const T *sig, int cols, int nslices, double eps, void *keys_ws,
-                         double *scal, int *ranks, int64_t *offsets, cudaStream_t st);
+cudaError_t complete_vectors(const T *Ahat, int64_t n1, int64_t n2, int64_t nslices,
+                             bool transposed, int64_t k_uniform, const int *ranks,
+                             const int64_t *offsets, int64_t max_rank, T *U, const T *S, T *V,
+                             cudaStream_t st);
+// After the restricted Jacobi of the second pass (entries desc[0..count-1], Zr in place of
+// the other side, R, sig and perm in the entry): the other side's columns Zr(:, perm q) /
+// sig_q into Otmp, the emitted side rotated, K R(:, perm q), into Ktmp, sig_q into S.
+template <typename T>
+cudaError_t rotate_back(const SliceDesc *desc, const int64_t *off, int count, int max_rho,
+                        int64_t kd, int64_t od, const T *Kin, T *Ktmp, T *Otmp, T *S,
+                        cudaStream_t st);
+// Sign rule after complete_vectors on transposed slices: the largest-magnitude entry of
+// each U column positive (ties: the first), V flipped with it; a zero U column takes the
+// sign of its V column.
+template <typename T>
+cudaError_t emit_signfix(int64_t n1, int64_t n2, int64_t nslices, int64_t k_uniform,
+                         const int *ranks, const int64_t *offsets, int64_t max_rank, T *U, T *V,
+                         cudaStream_t st);
+
+// t-SVDM-II selection (Algorithm 2) on the sorted singular values sig (cols x nslices),
+// over the whole GPU (select_launches kernels and one memset).  ws holds
+// select_workspace_bytes(cols, nslices) bytes; status (nullable) receives ST_NONFINITE for
+// NaN, infinite or negative values.
+size_t select_workspace_bytes(int64_t cols, int64_t nslices);
+int select_launches(bool fp64);
+template <typename T>
+cudaError_t select_ranks(const T *sig, int cols, int nslices, double eps, void *ws,
+                         double *scal, int *ranks, int64_t *offsets, int *status,
+                         cudaStream_t st);
 
 // The selection of one t-SVDM-II tensor of a batch (one CTA each).
 struct SelectSeg {

@@ -328,49 +328,108 @@ __device__ __forceinline__ void inner_pair(bool full, int step, int k, int &i, i
 }
 
 // Convergence test |g| > tol sqrt(a b)  <=>  g^2 > tol^2 a b (a, b >= 0), decided in FP64.
-// maybe_rotate is a conservative single-precision filter in front of it: it can only
-// reject pairs that are at least 2% below the threshold (single-precision products carry
-// relative errors ~1e-7), and defers to FP64 whenever a product over- or underflows.
+// decide64 puts single-precision products in front of the FP64 comparison: they carry
+// relative errors below 1e-6, so outside a 2% band around the threshold they give the FP64
+// answer, and the FP64 products run only inside the band (or when a single-precision
+// product over- or underflows).  The decision is always the FP64 one.
+__device__ __forceinline__ bool exceeds(double a, double b, double g, double tol2) {
+  return isfinite(a) && isfinite(b) && g * g > tol2 * (a * b);
+}
 template <typename T>
-__device__ __forceinline__ bool maybe_rotate(T a, T b, T g, double tol2) {
+__device__ __forceinline__ bool decide64(T a, T b, T g, double tol2) {
   const float af = (float)a, bf = (float)b, gf = (float)g;
   const float lhs = gf * gf, rhs = (float)tol2 * (af * bf);
-  if (!(lhs < 1e30f && rhs < 1e30f) || (rhs < 1e-30f && af != 0.f && bf != 0.f)) return true;
-  return lhs > 0.98f * rhs;
-}
-template <typename T>
-__device__ __forceinline__ bool exceeds(T a, T b, T g, double tol2) {
-  const double ad = (double)a, bd = (double)b, gd = (double)g;
-  return isfinite(ad) && isfinite(bd) && gd * gd > tol2 * (ad * bd);
+  if (lhs < 1e30f && rhs < 1e30f && rhs > 1e-30f) {
+    if (lhs < 0.98f * rhs) return false;
+    if (lhs > 1.02f * rhs) return true;
+  }
+  return exceeds((double)a, (double)b, (double)g, tol2);
 }
 
-// Single-precision form of the test for FP32 slices (the threshold tol ~ 4 sqrt(m) 2^-24
-// is itself a rounding-level quantity, so deciding it in FP32 moves it by ~1e-7
-// relative): g^2 > tol^2 a b while the products stay in the normal range, else the
-// overflow-free |g| > tol sqrt(a) sqrt(b).
+// Single-precision form of the test (the opt-in FP32 angle mode of FP32 slices; the
+// threshold tol ~ 4 sqrt(m) 2^-24 is itself a rounding-level quantity, so deciding it in
+// FP32 moves it by ~1e-7 relative): g^2 > tol^2 a b while the products stay in the normal
+// range, else the overflow-free |g| > tol sqrt(a) sqrt(b).
 __device__ __forceinline__ bool rot_test_f32(float a, float b, float g, float tol, float tol2) {
   const float lhs = g * g, rhs = tol2 * (a * b);
   if (lhs < 1e30f && rhs < 1e30f && rhs > 1e-30f) return lhs > rhs;
   return fabsf(g) > tol * (sqrtf(fmaxf(a, 0.f)) * sqrtf(fmaxf(b, 0.f)));
 }
 
+// a32: FP32 slices decide in FP32 (opt-in); otherwise, and always for FP64 slices, in FP64.
 template <typename T>
-__device__ __forceinline__ bool rot_test(T a, T b, T g, double tol, double tol2) {
-  if constexpr (sizeof(T) == 4)
-    return rot_test_f32(a, b, g, (float)tol, (float)tol2);
-  else
-    return maybe_rotate(a, b, g, tol2) && exceeds(a, b, g, tol2);
+__device__ __forceinline__ bool rot_test(T a, T b, T g, double tol, double tol2, bool a32) {
+  if constexpr (sizeof(T) == 4) {
+    if (a32) return rot_test_f32(a, b, g, (float)tol, (float)tol2);
+  }
+  return decide64(a, b, g, tol2);
+}
+
+// Rotation of a pair in FP64 from its Gram entries a = g_ii, b = g_jj, g = g_ij:
+//   zeta = (b - a) / (2 g);  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
+//     = sign(zeta) |2g| / (|b - a| + sqrt((b - a)^2 + 4 g^2))   (|t| <= 1),
+// c = 1 / sqrt(1 + t^2), s = c t, and the rotated diagonal a - t g, b + t g.
+__device__ __forceinline__ void angle64(double a, double b, double g, double &c, double &sn,
+                                        double &da, double &db) {
+  const double h = b - a, g2 = 2.0 * g;
+  double t = fabs(g2) / (fabs(h) + sqrt(fma(h, h, g2 * g2)));
+  if ((h >= 0.0) != (g2 >= 0.0)) t = -t;
+  c = rsqrt(fma(t, t, 1.0));
+  sn = c * t;
+  da = fma(-t, g, a);
+  db = fma(t, g, b);
+}
+
+// The FP64 rotation of an FP32 slice's pair, with few FP64 operations (the FP64 rate of the
+// GPU is a small fraction of its FP32 rate): FP32 estimates of t and c refined by one
+// Newton step each in FP64 arithmetic.  t solves g2 t^2 + 2 h t - g2 = 0 (the quadratic of
+// tan theta: t^2 + 2 zeta t - 1 = 0 times g2), whose derivative 2 (g2 t + h) has magnitude
+// 2 sqrt(h^2 + g2^2) at the root; from an estimate with absolute error d (|t| <= 1) the
+// step leaves an error of about d^2 / 2 plus the FP64 rounding of f(t0), so ~1e-13 from an
+// FP32 estimate.  c = (1 + t^2)^(-1/2) takes the Newton step c + c (1 - (1 + t^2) c^2) / 2
+// of the reciprocal square root.  s = c t and the rotated diagonal a - t g, b + t g follow
+// in FP64; the caller rounds the results to FP32.
+__device__ __forceinline__ void angle64_f32(float a, float b, float g, double &c, double &sn,
+                                            double &da, double &db) {
+  const float hf = b - a, g2f = 2.f * g;
+  float t0 = fabsf(g2f) / (fabsf(hf) + hypotf(hf, g2f));
+  if ((hf >= 0.f) != (g2f >= 0.f)) t0 = -t0;
+  const double ad = a, bd = b, gd = g, g2 = 2.0 * gd, h = bd - ad, td = t0;
+  const double f = fma(g2, td * td, fma(2.0 * h, td, -g2));      // g2 t^2 + 2 h t - g2
+  const float fp = 2.f * fmaf(g2f, t0, hf);                      // f'(t0), FP32 suffices
+  const float rf = __frcp_rn(fp);     // |f'| >= 2 |g2| > 0; infinite only for denormal pairs
+  const double t = isfinite(rf) ? fma(-f, (double)rf, td) : td;
+  const double u = fma(t, t, 1.0);
+  const float c0f = __frsqrt_rn((float)u);
+  const double c0 = c0f;
+  const double e = fma(-u, c0 * c0, 1.0);
+  c = fma((double)(0.5f * c0f), e, c0);
+  sn = c * t;
+  da = fma(-t, gd, ad);
+  db = fma(t, gd, bd);
+}
+
+// The same rotation in FP32 (the opt-in FP32 angle mode).  c is the correctly rounded
+// 1/sqrt: an approximate reciprocal square root biased c (and the column norms, over
+// thousands of rotations) by ~1e-5.
+__device__ __forceinline__ void angle32(float a, float b, float g, float &c, float &sn,
+                                        float &da, float &db) {
+  const float h = b - a, g2 = 2.f * g;
+  float t = fabsf(g2) / (fabsf(h) + hypotf(h, g2));
+  if ((h >= 0.f) != (g2 >= 0.f)) t = -t;
+  c = __frsqrt_rn(fmaf(t, t, 1.f));
+  sn = c * t;
+  da = fmaf(-t, g, a);
+  db = fmaf(t, g, b);
 }
 
 // Rotation of one pair from its current Gram entries (a = g_ii, b = g_jj, g = g_ij),
-// stored in slot `sl` as pair k.  FP32 slices take the angle in FP32 (as the classical
-// single-precision one-sided Jacobi does: the rotation is applied to freshly formed
-// Grams, so the angle's rounding only affects the convergence rate); FP64 slices in FP64.
-//   zeta = (b - a) / (2 g);  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
-//     = sign(zeta) |2g| / (|b - a| + sqrt((b - a)^2 + 4 g^2))   (|t| <= 1)
+// stored in slot `sl` as pair k.  The test and the angle run in FP64 (from the FP32 Gram
+// entries of an FP32 slice, the results rounded to FP32), or in FP32 when a32 is set for
+// an FP32 slice.
 template <typename T, int W2, int NS, typename SM>
 __device__ __forceinline__ void pair_angle(SM &s, int sl, int k, int i, int j, T a, T b, T g,
-                                           double tol, double tol2) {
+                                           double tol, double tol2, bool a32) {
   s.pi[sl][k] = i;
   s.pj[sl][k] = j;
   s.pos[sl][i] = 2 * k;
@@ -378,27 +437,29 @@ __device__ __forceinline__ void pair_angle(SM &s, int sl, int k, int i, int j, T
   int rot = 0;
   if (!(isfinite(a) && isfinite(b))) {
     s.nonfinite = 1;
-  } else if (rot_test(a, b, g, tol, tol2)) {
+  } else if (rot_test(a, b, g, tol, tol2, a32)) {
+    bool done = false;
     if constexpr (sizeof(T) == 4) {
-      const float h = b - a, g2 = 2.f * g;
-      float t = fabsf(g2) / (fabsf(h) + hypotf(h, g2));
-      if ((h >= 0.f) != (g2 >= 0.f)) t = -t;
-      // correctly rounded 1/sqrt: an approximate reciprocal square root biased c (and the
-      // column norms, over thousands of rotations) by ~1e-5
-      const float c = __frsqrt_rn(fmaf(t, t, 1.f));
-      s.cs[sl][2 * k] = c;
-      s.cs[sl][2 * k + 1] = c * t;
-      s.dd[sl][2 * k] = fmaf(-t, g, a);
-      s.dd[sl][2 * k + 1] = fmaf(t, g, b);
-    } else {
-      const double h = b - a, g2 = 2.0 * g;
-      const double sgn = ((h >= 0.0) == (g2 >= 0.0)) ? 1.0 : -1.0;
-      const double t = sgn * fabs(g2) / (fabs(h) + sqrt(h * h + g2 * g2));
-      const double c = rsqrt(1.0 + t * t);
+      if (a32) {
+        float c, sn, da, db;
+        angle32(a, b, g, c, sn, da, db);
+        s.cs[sl][2 * k] = c;
+        s.cs[sl][2 * k + 1] = sn;
+        s.dd[sl][2 * k] = da;
+        s.dd[sl][2 * k + 1] = db;
+        done = true;
+      }
+    }
+    if (!done) {
+      double c, sn, da, db;
+      if constexpr (sizeof(T) == 4)
+        angle64_f32(a, b, g, c, sn, da, db);
+      else
+        angle64(a, b, g, c, sn, da, db);
       s.cs[sl][2 * k] = (T)c;
-      s.cs[sl][2 * k + 1] = (T)(c * t);
-      s.dd[sl][2 * k] = (T)(a - t * g);
-      s.dd[sl][2 * k + 1] = (T)(b + t * g);
+      s.cs[sl][2 * k + 1] = (T)sn;
+      s.dd[sl][2 * k] = (T)da;
+      s.dd[sl][2 * k + 1] = (T)db;
     }
     rot = 1;
     s.any_rot = 1;
@@ -420,8 +481,8 @@ __device__ __forceinline__ void pair_angle(SM &s, int sl, int k, int i, int j, T
 // from the Gram before step s and the rotations of step s, with the same 2 x 2
 // arithmetic the update warps use, so both see bit-identical entries.
 template <typename T, int W2, int NS, typename SM, typename Bar>
-__device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, const Bar &bar) {
-  
+__device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, const Bar &bar,
+                            bool a32) {
   constexpr int NP = W2 / 2;
   constexpr int AW = NT / 32 - 1;          // the angle warp
   constexpr int NU = NT - 32;              // update threads
@@ -433,7 +494,7 @@ __device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, c
     int i = idx / W2, j = idx % W2;
     if (i < j && (full || (i < NP && j >= NP))) {
       const T a = s.G[g0][tri<W2>(i, i)], b = s.G[g0][tri<W2>(j, j)], g = s.G[g0][tri<W2>(i, j)];
-      if (rot_test(a, b, g, tol, tol2)) need = 1;
+      if (rot_test(a, b, g, tol, tol2, a32)) need = 1;
     }
   }
   bar.sync();                        // every thread has read step_rot of the previous call
@@ -471,7 +532,7 @@ __device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, c
     int i, j;
     inner_pair<W2>(full, 0, lane, i, j);
     pair_angle<T, W2, NS>(s, 0, lane, i, j, s.G[g0][tri<W2>(i, i)], s.G[g0][tri<W2>(j, j)],
-                          s.G[g0][tri<W2>(i, j)], tol, tol2);
+                          s.G[g0][tri<W2>(i, j)], tol, tol2, a32);
   }
   bar.sync();
   for (int step = 0; step < nsteps; ++step) {
@@ -501,7 +562,7 @@ __device__ void inner_sweep(SM &s, double tol, bool full, bool first, int tid, c
                     s.cs[sl][2 * ph + 1], o[0], o[1], o[2], o[3]);
           g = o[2 * rl + rh];
         }
-        pair_angle<T, W2, NS>(s, sl ^ 1, lane, i, j, a, b, g, tol, tol2);
+        pair_angle<T, W2, NS>(s, sl ^ 1, lane, i, j, a, b, g, tol, tol2, a32);
       }
     } else {
       // G_{s+1} = J^T G_s J on the blocks pp <= qq (the rest is their transpose)
@@ -941,21 +1002,28 @@ __device__ void apply_tc(SmemTc &s, float *__restrict__ W, int rows, int lda, ui
 }
 
 // Rotation of pair k from its Gram entries a = g_ii, b = g_jj, g = g_ij (FP32 slices): the
-// test and angle of pair_angle, stored in slot `sl` (c, s; rotated diagonal; flag).
+// test and angle of pair_angle (FP64, or FP32 when a32), stored in slot `sl` (c, s;
+// rotated diagonal; flag).
 __device__ __forceinline__ void cross_angle(SmemTc &s, int sl, int k, float a, float b, float g,
-                                            float tol, float tol2) {
+                                            float tol, float tol2, double tol2d, bool a32) {
   int rot = 0;
   float c = 1.f, sn = 0.f;
   if (!(isfinite(a) && isfinite(b))) {
     s.nonfinite = 1;
-  } else if (rot_test_f32(a, b, g, tol, tol2)) {
-    const float h = b - a, g2 = 2.f * g;
-    float t = fabsf(g2) / (fabsf(h) + hypotf(h, g2));
-    if ((h >= 0.f) != (g2 >= 0.f)) t = -t;
-    c = __frsqrt_rn(fmaf(t, t, 1.f));
-    sn = c * t;
-    s.dd[sl][2 * k] = fmaf(-t, g, a);
-    s.dd[sl][2 * k + 1] = fmaf(t, g, b);
+  } else if (a32 ? rot_test_f32(a, b, g, tol, tol2) : decide64(a, b, g, tol2d)) {
+    float da, db;
+    if (a32) {
+      angle32(a, b, g, c, sn, da, db);
+    } else {
+      double cd, sd, dad, dbd;
+      angle64_f32(a, b, g, cd, sd, dad, dbd);
+      c = (float)cd;
+      sn = (float)sd;
+      da = (float)dad;
+      db = (float)dbd;
+    }
+    s.dd[sl][2 * k] = da;
+    s.dd[sl][2 * k + 1] = db;
     rot = 1;
     s.any_rot = 1;
     s.step_rot = 1;
@@ -1018,7 +1086,7 @@ __device__ __forceinline__ void cross_q_item(SmemTc &s, const float2 *cs2, int i
 // warps).  One barrier per step.  With row stride 33 the loads and stores of a warp's
 // blocks fall on distinct banks.
 __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
-                                  const GroupBar &bar) {
+                                  const GroupBar &bar, bool a32) {
   constexpr int W2 = SmemTc::W2;
   constexpr int NP = W2 / 2;
   constexpr int NB = NP * (NP + 1) / 2;
@@ -1035,12 +1103,14 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
   static_assert(3 * QW + 32 == NP * (W2 / 4), "Q item split");
   float *A = s.X3[0], *B = s.X3[1], *C = s.X3[2];
   const float tolf = (float)tol, tol2f = (float)(tol * tol);
+  const double tol2d = tol * tol;
   const int warp = tid >> 5, lane = tid & 31;
   // fresh-Gram convergence test |g| > tol sqrt(a b) over the cross pairs
   int need = 0;
   for (int idx = tid; idx < NP * NP; idx += NT) {
     const int i = idx >> 5, j = idx & 31;
-    if (rot_test_f32(A[i * XLD + i], C[j * XLD + j], B[i * XLD + j], tolf, tol2f)) need = 1;
+    const float a = A[i * XLD + i], b = C[j * XLD + j], g = B[i * XLD + j];
+    if (a32 ? rot_test_f32(a, b, g, tolf, tol2f) : decide64(a, b, g, tol2d)) need = 1;
   }
   bar.sync();                        // every thread has read step_rot of the previous call
   if (tid == 0) {
@@ -1067,7 +1137,7 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
   const int kq = (lane + 1) & 31;
   if (warp == AW)                    // rotations of step 0: pair k = columns k, 32 + k
     cross_angle(s, 0, lane, A[lane * XLD + lane], C[lane * XLD + lane], B[lane * XLD + lane],
-                tolf, tol2f);
+                tolf, tol2f, tol2d, a32);
   bar.sync();
   for (int step = 0; step < NP; ++step) {
     const int sl = step & 1;
@@ -1093,7 +1163,8 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
           const int skq = (kq + step) & 31;
           const float a = s.rot[sl][lane] ? s.dd[sl][2 * lane] : A[lane * XLD + lane];
           const float b = s.rot[sl][kq] ? s.dd[sl][2 * kq + 1] : C[skq * XLD + skq];
-          cross_angle(s, sl ^ 1, lane, a, b, lane < NP - 1 ? o01 : o10, tolf, tol2f);
+          cross_angle(s, sl ^ 1, lane, a, b, lane < NP - 1 ? o01 : o10, tolf, tol2f, tol2d,
+                      a32);
         }
       }
     } else {
@@ -1231,7 +1302,7 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
 
     // V = I (this CTA initialises columns crank, crank + csize, ...); a warm start keeps the
     // caller's V (the slice then holds W V)
-    if (!p.warm)
+    if (!p.warm && !p.novec)
       for (int c = crank; c < v.cols; c += csize)
         for (int r = tid; r < v.cols; r += NT)
           __stcg(v.V + (int64_t)c * v.cols + r, r == c ? T(1) : T(0));
@@ -1254,7 +1325,7 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
           __syncthreads();
           gram<T, W2, NS>(s, v.W, v.rows, v.rows);
           for (int is = 0; is < p.inner_sweeps; ++is) {
-            inner_sweep<T, W2, NS>(s, tol, round == 0, is == 0, tid, bar);
+            inner_sweep<T, W2, NS>(s, tol, round == 0, is == 0, tid, bar, p.angle32 != 0);
             if (!s.step_rot) break;
           }
           __syncthreads();
@@ -1263,7 +1334,7 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
           if (s.any_rot) {
             if (tid == 0) s.sweep_any = 1;
             apply_q<T, W2, NS>(s, v.W, v.rows, v.rows);
-            apply_q<T, W2, NS>(s, v.V, v.cols, v.cols);
+            if (!p.novec) apply_q<T, W2, NS>(s, v.V, v.cols, v.cols);
           }
           __syncthreads();
         }
@@ -1384,7 +1455,12 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
   SmemTc *groups =
       reinterpret_cast<SmemTc *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
+  // the inner sweeps see the group's warps rotated by g, so that their angle warp (the
+  // last one) is physical warp 7 - g: the three groups' angle warps, which carry the FP64
+  // angle arithmetic, sit on different SM sub-partitions
+  const int vtid = (tid + 32 * g) % NT;
   SmemTc &s = groups[g];
+  const unsigned spin = p.wait_polls > 0 ? (unsigned)p.wait_polls : SCHED_SPIN;
   const GroupBar gbar{1 + g};
   const double tol = p.tol;
   SchedHdr *hdr = reinterpret_cast<SchedHdr *>(p.sched);
@@ -1444,7 +1520,7 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
           break;
         }
         if (vload(&hdr->fin) >= p.nslices) break;
-        if (idle >= SCHED_SPIN) {
+        if (idle >= spin) {
           atomicExch(&hdr->abort, 1);
           s.fail = 1;
           break;
@@ -1463,7 +1539,7 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
     const SliceView<float> v = slice_view<float>(p, slice);
     if (kind == WK_START) {
       // V = I (a warm start keeps the caller's V), then open sweep 1
-      if (!p.warm)
+      if (!p.warm && !p.novec)
         for (int c = 0; c < v.cols; ++c)
           for (int r = tid; r < v.cols; r += NT)
             __stcg(v.V + (int64_t)c * v.cols + r, r == c ? 1.f : 0.f);
@@ -1493,7 +1569,7 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
       const int *vi = ver + (int64_t)slice * nbmax + bi, *vj = ver + (int64_t)slice * nbmax + bj;
       for (unsigned it = 0; vload(vi) < need || vload(vj) < need; ++it) {
         if (vload(&hdr->abort)) break;
-        if (it >= SCHED_SPIN) {
+        if (it >= spin) {
           atomicExch(&hdr->abort, 1);
           s.fail = 1;
           break;
@@ -1512,9 +1588,9 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
     gram_tc(s, v.W, v.rows, v.rows, phase, tid, gbar, cross);
     for (int is = 0; is < p.inner_sweeps; ++is) {
       if (cross)
-        inner_sweep_cross(s, tol, is == 0, tid, gbar);
+        inner_sweep_cross(s, tol, is == 0, vtid, gbar, p.angle32 != 0);
       else
-        inner_sweep<float, W2, 2>(s, tol, true, is == 0, tid, gbar);
+        inner_sweep<float, W2, 2>(s, tol, true, is == 0, vtid, gbar, p.angle32 != 0);
       if (!s.step_rot) break;
     }
     gbar.sync();
@@ -1526,7 +1602,7 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
     if (s.any_rot) {
       build_bq(s, tid, gbar);
       apply_tc(s, v.W, v.rows, v.rows, phase, tid, gbar);
-      apply_tc(s, v.V, v.cols, v.cols, phase, tid, gbar);
+      if (!p.novec) apply_tc(s, v.V, v.cols, v.cols, phase, tid, gbar);
     }
     __threadfence();
     gbar.sync();
@@ -1744,7 +1820,40 @@ __global__ void __launch_bounds__(256) emit_kernel(const T *__restrict__ A, int6
   const int j = perm[(int64_t)slice * cols + q];
   const T sg = sig[(int64_t)slice * cols + q];
   const T *wcol = A + (int64_t)slice * sA + (int64_t)j * rows;     // rows entries, scaled 1/sg
-  const T *zcol = Vw + (int64_t)slice * sV + (int64_t)j * cols;    // cols entries
+  const T *zcol = Vw ? Vw + (int64_t)slice * sV + (int64_t)j * cols : nullptr;   // cols entries
+  if (!Vw) {
+    // no right vectors: the work matrix's side only (U of a non-transposed slice, sign-fixed
+    // on itself; V of a transposed one, sign decided after the other side is formed)
+    __shared__ T k_bv[8];
+    __shared__ int k_bi[8];
+    __shared__ T k_sign;
+    const T inv0 = sg > T(0) ? T(1) / sg : T(0);
+    T bv0 = T(-1);
+    int bi0 = 0x7fffffff;
+    if (!transposed)
+      for (int a = threadIdx.x; a < rows; a += blockDim.x) argmax_abs(wcol[a] * inv0, a, bv0, bi0);
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, bv0, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi0, o);
+      merge_max(ov, oi, bv0, bi0);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      k_bv[threadIdx.x >> 5] = bv0;
+      k_bi[threadIdx.x >> 5] = bi0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T b = T(-1);
+      int i = 0x7fffffff;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) merge_max(k_bv[w], k_bi[w], b, i);
+      k_sign = (b > T(0) && wcol[i] * inv0 < T(0)) ? T(-1) : T(1);
+      S[colbase + q] = sg;
+    }
+    __syncthreads();
+    T *out = transposed ? V + (colbase + q) * rows : U + (colbase + q) * rows;
+    for (int a = threadIdx.x; a < rows; a += blockDim.x) out[a] = k_sign * (wcol[a] * inv0);
+    return;
+  }
   const T inv = sg > T(0) ? T(1) / sg : T(0);
   // left vector: W-part (non-transposed) or Z-part (transposed)
   const int nl = transposed ? cols : rows;

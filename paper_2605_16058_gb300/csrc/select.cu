@@ -12,13 +12,22 @@
 // Here:
 //   1. per slice, the FP64 sums of sigma^2 over each tail j..cols-1 (ascending order is the
 //      tail of the descending slice), and their total;
-//   2. a bisection over the key bits for the largest key k with (S(k) + val(k)) / sum(v)
+//   2. a search over the key bits for the largest key k with (S(k) + val(k)) / sum(v)
 //      < eps^2, where S(k) adds each slice's tail below k (binary search in the slice);
 //   3. tau = the largest present key <= k; rho_i, the discarded sum and the offsets
 //      (exclusive prefix sum of rho, int64) from one binary search per slice.
 // All sums are FP64 in a fixed order, so a result is reproducible run to run; against the
-// sorted running sum of Algorithm 2 it differs only by FP64 summation order.  One CTA per
-// selection: the work is a few hundred slices times ~32 bisection steps of a binary search.
+// sorted running sum of Algorithm 2 it differs only by FP64 summation order.
+//
+// One tensor (select_ranks) runs over the whole GPU: a warp per slice forms the tail sums,
+// then each search launch splits the key interval into 16 and evaluates the 15 inner keys
+// over all slices (CTAs take disjoint slice ranges; the last CTA to finish adds their
+// partial sums in CTA order and narrows the interval, so no CTA ever waits for another),
+// and one CTA finishes steps 3.  The tensors of a batch (select_segments) take one CTA each.
+// Singular values that are NaN, infinite or negative (-0 counts as 0) make the selection
+// report NaN sums, zero ranks and offsets, and the non-finite status bit.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tsvdm {
@@ -30,7 +39,9 @@ constexpr int NW = ST / 32;
 template <typename T> struct KeyOf;
 template <> struct KeyOf<float> {
   using K = unsigned int;
-  __device__ static K key(float s) { return __float_as_uint(s); }
+  static constexpr K KINF = 0x7f800000u;     // key of +inf: no finite value reaches it
+  static constexpr int ROUNDS = 8;           // 16-way search rounds that narrow [0, KINF] to 1
+  __device__ static K key(float s) { return __float_as_uint(fabsf(s)); }
   __device__ static double val(K k) {
     double s = (double)__uint_as_float(k);
     return s * s;
@@ -38,12 +49,19 @@ template <> struct KeyOf<float> {
 };
 template <> struct KeyOf<double> {
   using K = unsigned long long;
+  static constexpr K KINF = 0x7ff0000000000000ull;
+  static constexpr int ROUNDS = 16;
   __device__ static K key(double s) { return (K)__double_as_longlong(s * s); }
   __device__ static double val(K k) { return __longlong_as_double((long long)k); }
 };
 
+template <typename T>
+__device__ __forceinline__ bool bad_value(T x) {
+  return !(x >= T(0)) || isinf(x);      // NaN, negative or infinite (-0 passes)
+}
+
 // Block-wide inclusive scan of one int64 per thread, fixed order; *total receives the
-// block sum.
+// block sum.  (Blocks of ST threads.)
 __device__ long long block_scan_ll(long long v, long long *wsum, long long *total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -70,6 +88,7 @@ __device__ long long block_scan_ll(long long v, long long *wsum, long long *tota
 }
 
 // Fixed-order block reduction of one double per thread (every thread gets the sum).
+template <int NWARPS>
 __device__ double block_sum(double v, double *wsum) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -77,7 +96,7 @@ __device__ double block_sum(double v, double *wsum) {
   if (lane == 0) wsum[warp] = v;
   __syncthreads();
   double t = 0.0;
-  for (int w = 0; w < NW; ++w) t += wsum[w];
+  for (int w = 0; w < NWARPS; ++w) t += wsum[w];
   __syncthreads();
   return t;
 }
@@ -104,38 +123,39 @@ __device__ __forceinline__ int first_below(const T *s, int cols, typename KeyOf<
   int lo = 0, hi = cols;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (KeyOf<T>::key(s[mid]) >= k) lo = mid + 1;
+    if (KeyOf<T>::key(__ldg(s + mid)) >= k) lo = mid + 1;
     else hi = mid;
   }
   return lo;
 }
 
+// Steps 3 of the selection, given the tail sums, the total and the search result `lo`
+// (the largest key whose Algorithm 2 inequality holds; used when eps^2 in (0, 1)).
+// One block of ST threads.
 template <typename T>
-__device__ void select_body(const T *__restrict__ sig, int cols, int nslices, double eps,
-                            void *kws, double *scal, int *ranks, int64_t *offsets) {
+__device__ void select_finish(const T *__restrict__ sig, int cols, int nslices, double eps2,
+                              const double *tail, double total, typename KeyOf<T>::K lo,
+                              bool bad, double *scal, int *ranks, int64_t *offsets,
+                              int *status) {
   using KO = KeyOf<T>;
   using K = typename KO::K;
-  // key of +inf: no finite singular value reaches it
-  constexpr K KINF = sizeof(K) == 4 ? K(0x7f800000u) : K(0x7ff0000000000000ull);
   __shared__ double wsum[NW];
   __shared__ long long wsum_ll[NW];
   __shared__ K wkey[NW];
   const int tid = threadIdx.x;
-  // tail[i * cols + j] = sum of sigma_{j',i}^2 for j' >= j (the cols - j smallest of slice i)
-  double *tail = reinterpret_cast<double *>(kws);
-  double part = 0.0;
-  for (int i = tid; i < nslices; i += ST) {
-    const T *s = sig + (int64_t)i * cols;
-    double *t = tail + (int64_t)i * cols;
-    double run = 0.0;
-    for (int j = cols - 1; j >= 0; --j) {
-      run += KO::val(KO::key(s[j]));
-      t[j] = run;
+  if (bad) {
+    for (int i = tid; i < nslices; i += ST) {
+      ranks[i] = 0;
+      offsets[i] = 0;
     }
-    part += run;
+    if (tid == 0) {
+      offsets[nslices] = 0;
+      scal[SC_TOTAL] = scal[SC_DISCARD] = scal[SC_TAU] = scal[SC_TOTRANK] = __longlong_as_double(
+          0x7ff8000000000000ll);
+      if (status) atomicOr(status, ST_NONFINITE);
+    }
+    return;
   }
-  const double total = block_sum(part, wsum);
-  const double eps2 = eps * eps;
   bool has_tau = false;
   K tau = K(0);
   if (total == 0.0) {
@@ -169,7 +189,7 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
           found = 1;
         }
       }
-      copies = block_sum(copies, wsum);
+      copies = block_sum<NW>(copies, wsum);
       found = __syncthreads_or(found);
       second = block_max<K>(second, wkey);
       if (copies >= 2.0) {
@@ -181,22 +201,6 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
       }
     }
   } else if (eps2 > 0.0) {
-    // largest key k with (S(k) + val(k)) / total < eps^2 (Algorithm 2's own comparison):
-    // true at k = 0, false at +inf
-    K lo = 0, hi = KINF;
-    while (hi - lo > 1) {
-      const K mid = lo + (hi - lo) / 2;
-      double below = 0.0;
-      for (int i = tid; i < nslices; i += ST) {
-        const int c = first_below(sig + (int64_t)i * cols, cols, mid);
-        if (c < cols) below += tail[(int64_t)i * cols + c];
-      }
-      const double S = block_sum(below, wsum);
-      if ((S + KO::val(mid)) / total < eps2)
-        lo = mid;
-      else
-        hi = mid;
-    }
     // tau = the largest present key <= lo (none: J = 0, nothing is discarded)
     K best = K(0);
     int found = 0;
@@ -236,7 +240,7 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
     if (i < nslices) offsets[i] = carry_ll + incl - r;
     carry_ll += tot_ll;
   }
-  const double d = block_sum(disc, wsum);
+  const double d = block_sum<NW>(disc, wsum);
   if (tid == 0) {
     offsets[nslices] = carry_ll;
     scal[SC_TOTAL] = total;
@@ -244,6 +248,213 @@ __device__ void select_body(const T *__restrict__ sig, int cols, int nslices, do
     scal[SC_TAU] = (has_tau && total > 0.0) ? KO::val(tau) : -1.0;
     scal[SC_TOTRANK] = (double)carry_ll;
   }
+}
+
+// The whole selection of one tensor in one block (a batch segment).
+template <typename T>
+__device__ void select_body(const T *__restrict__ sig, int cols, int nslices, double eps,
+                            void *kws, double *scal, int *ranks, int64_t *offsets) {
+  using KO = KeyOf<T>;
+  using K = typename KO::K;
+  __shared__ double wsum[NW];
+  const int tid = threadIdx.x;
+  // tail[i * cols + j] = sum of sigma_{j',i}^2 for j' >= j (the cols - j smallest of slice i)
+  double *tail = reinterpret_cast<double *>(kws);
+  double part = 0.0;
+  int bad = 0;
+  for (int i = tid; i < nslices; i += ST) {
+    const T *s = sig + (int64_t)i * cols;
+    double *t = tail + (int64_t)i * cols;
+    double run = 0.0;
+    for (int j = cols - 1; j >= 0; --j) {
+      const T x = s[j];
+      bad |= bad_value(x);
+      run += KO::val(KO::key(x));
+      t[j] = run;
+    }
+    part += run;
+  }
+  bad = __syncthreads_or(bad);
+  const double total = block_sum<NW>(part, wsum);
+  const double eps2 = eps * eps;
+  K lo = 0, hi = KO::KINF;
+  if (!bad && total != 0.0 && eps2 > 0.0 && eps2 < 1.0) {
+    // largest key k with (S(k) + val(k)) / total < eps^2 (Algorithm 2's own comparison):
+    // true at k = 0, false at +inf
+    while (hi - lo > 1) {
+      const K mid = lo + (hi - lo) / 2;
+      double below = 0.0;
+      for (int i = tid; i < nslices; i += ST) {
+        const int c = first_below(sig + (int64_t)i * cols, cols, mid);
+        if (c < cols) below += tail[(int64_t)i * cols + c];
+      }
+      const double S = block_sum<NW>(below, wsum);
+      if ((S + KO::val(mid)) / total < eps2)
+        lo = mid;
+      else
+        hi = mid;
+    }
+  }
+  select_finish<T>(sig, cols, nslices, eps2, tail, total, lo, bad != 0, scal, ranks, offsets,
+                   nullptr);
+}
+
+// ---------------------------------------------------------------- one tensor, whole GPU
+// Search state after the tail sums (in the workspace, behind the tail sums and partials).
+struct SelState {
+  unsigned long long lo, hi;   // the search interval (keys)
+  double total;                // sum of all sigma^2
+  int bad;                     // a NaN, infinite or negative value was seen
+  int search;                  // 1: eps^2 in (0, 1) and total > 0, the key search runs
+  unsigned int arrive;         // CTAs finished with the current launch
+  int pad[9];
+};
+constexpr int SEL_WARPS = 8;               // slices per tail CTA (a warp each)
+constexpr int SEL_CAND = 16;               // key interval split per search launch
+constexpr int SEL_SLICE_LANES = 256 / SEL_CAND;
+constexpr int SEL_MAX_CTAS = 1024;
+
+// Last-CTA detection: true in every thread of the CTA that finishes the launch last, after
+// which it sees every other CTA's results.
+__device__ __forceinline__ bool last_cta(SelState *st) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&st->arrive, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// 1. Tail sums, a warp per slice: the 32 lanes take contiguous chunks, sum them from the
+// end, and the chunk sums are combined by a suffix scan across the lanes (fixed order).
+template <typename T>
+__global__ void __launch_bounds__(256) sel_tails_kernel(const T *__restrict__ sig, int cols,
+                                                        int nslices, double eps2, double *tail,
+                                                        SelState *st) {
+  using KO = KeyOf<T>;
+  __shared__ double wsum[SEL_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * SEL_WARPS + warp;
+  int bad = 0;
+  if (i < nslices) {
+    const T *s = sig + (int64_t)i * cols;
+    double *t = tail + (int64_t)i * cols;
+    const int chunk = (cols + 31) / 32;
+    const int j0 = min(lane * chunk, cols), j1 = min(j0 + chunk, cols);
+    double csum = 0.0;
+    for (int j = j1 - 1; j >= j0; --j) {
+      const T x = s[j];
+      bad |= bad_value(x);
+      csum += KO::val(KO::key(x));
+    }
+    // inclusive suffix sums of the chunk sums (lane l: chunks l..31), then exclusive
+    double incl = csum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double u = __shfl_down_sync(0xffffffffu, incl, o);
+      if (lane + o < 32) incl += u;
+    }
+    double run = __shfl_down_sync(0xffffffffu, incl, 1);
+    if (lane == 31) run = 0.0;
+    for (int j = j1 - 1; j >= j0; --j) {
+      run += KO::val(KO::key(s[j]));
+      t[j] = run;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
+  if (!last_cta(st)) return;
+  // the total over the slices' tails, in slice order per thread, then a fixed tree
+  double part = 0.0;
+  for (int k = threadIdx.x; k < nslices; k += 256) part += tail[(int64_t)k * cols];
+  const double total = block_sum<SEL_WARPS>(part, wsum);
+  if (threadIdx.x == 0) {
+    st->total = total;
+    st->lo = 0;
+    st->hi = KO::KINF;
+    st->search = (total != 0.0 && eps2 > 0.0 && eps2 < 1.0 && !*(volatile int *)&st->bad) ? 1 : 0;
+    st->arrive = 0;
+  }
+}
+
+// 2. One 16-way search round: the keys c_1 < ... < c_15 inside (lo, hi) split it into 16
+// (or lo + 1 .. hi - 1 when it is narrower); S(c_m) is summed over the CTAs' slice ranges
+// (thread = candidate x slice lane, slices of a lane in increasing order, then the lanes in
+// order, then the CTAs in order), and the last CTA keeps the sub-interval where Algorithm
+// 2's inequality changes from true to false.
+template <typename T>
+__global__ void __launch_bounds__(256) sel_round_kernel(const T *__restrict__ sig, int cols,
+                                                        int nslices, double eps2,
+                                                        const double *tail, double *part,
+                                                        SelState *st, int per_cta) {
+  using KO = KeyOf<T>;
+  using K = typename KO::K;
+  __shared__ double red[SEL_CAND][SEL_SLICE_LANES + 1];
+  __shared__ int holds[SEL_CAND];
+  const K lo = (K)st->lo, hi = (K)st->hi;
+  if (!st->search || hi - lo <= 1) return;      // uniform across the grid
+  const K span = hi - lo;
+  const int nc = span >= SEL_CAND ? SEL_CAND - 1 : (int)(span - 1);
+  auto cand = [&](int m) -> K {                  // m = 1 .. nc
+    if (span >= SEL_CAND) return lo + (span / SEL_CAND) * m + ((span % SEL_CAND) * m) / SEL_CAND;
+    return lo + (K)m;
+  };
+  const int m = (threadIdx.x % SEL_CAND) + 1, sl = threadIdx.x / SEL_CAND;
+  const int i0 = blockIdx.x * per_cta, i1 = min(i0 + per_cta, nslices);
+  double acc = 0.0;
+  if (m <= nc) {
+    const K c = cand(m);
+    for (int i = i0 + sl; i < i1; i += SEL_SLICE_LANES) {
+      const int j = first_below(sig + (int64_t)i * cols, cols, c);
+      if (j < cols) acc += tail[(int64_t)i * cols + j];
+    }
+  }
+  red[m - 1][sl] = acc;
+  __syncthreads();
+  if (threadIdx.x < SEL_CAND) {
+    double s = 0.0;
+    for (int q = 0; q < SEL_SLICE_LANES; ++q) s += red[threadIdx.x][q];
+    part[(int64_t)blockIdx.x * SEL_CAND + threadIdx.x] = s;
+  }
+  if (!last_cta(st)) return;
+  if (threadIdx.x < SEL_CAND) {
+    const int mm = threadIdx.x + 1;
+    int h = 0;
+    if (mm <= nc) {
+      double S = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) S += part[(int64_t)b * SEL_CAND + threadIdx.x];
+      h = (S + KO::val(cand(mm))) / st->total < eps2;
+    }
+    holds[threadIdx.x] = h;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the inequality holds for c_1 .. c_q and fails from c_{q+1} on (it only grows with k)
+    int q = 0;
+    while (q < nc && holds[q]) ++q;
+    st->lo = q > 0 ? (unsigned long long)cand(q) : (unsigned long long)lo;
+    st->hi = q < nc ? (unsigned long long)cand(q + 1) : (unsigned long long)hi;
+    st->arrive = 0;
+  }
+}
+
+// 3. tau, ranks, offsets, discarded sum (one block).
+template <typename T>
+__global__ void __launch_bounds__(ST, 1) sel_finish_kernel(const T *__restrict__ sig, int cols,
+                                                           int nslices, double eps2,
+                                                           const double *tail, SelState *st,
+                                                           double *scal, int *ranks,
+                                                           int64_t *offsets, int *status) {
+  using K = typename KeyOf<T>::K;
+  select_finish<T>(sig, cols, nslices, eps2, tail, st->total, (K)st->lo, st->bad != 0, scal,
+                   ranks, offsets, status);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(ST, 1) select_seg_kernel(const SelectSeg *segs) {
+  const SelectSeg g = segs[blockIdx.x];
+  select_body<T>(reinterpret_cast<const T *>(g.sig), g.cols, g.nslices, g.eps, g.keys, g.scal,
+                 g.ranks, g.offsets);
 }
 
 // t-SVDM-I truncation sums: total = sum of all sigma^2, discarded = sum over j >= k.
@@ -281,23 +492,16 @@ __global__ void __launch_bounds__(ST) trunc_sums_kernel(const T *__restrict__ si
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(ST, 1) select_kernel(const T *__restrict__ sig, int cols,
-                                                       int nslices, double eps, void *kws,
-                                                       double *scal, int *ranks,
-                                                       int64_t *offsets) {
-  select_body<T>(sig, cols, nslices, eps, kws, scal, ranks, offsets);
-}
-
-// One CTA per segment (one t-SVDM-II tensor of a batch).
-template <typename T>
-__global__ void __launch_bounds__(ST, 1) select_seg_kernel(const SelectSeg *segs) {
-  const SelectSeg g = segs[blockIdx.x];
-  select_body<T>(reinterpret_cast<const T *>(g.sig), g.cols, g.nslices, g.eps, g.keys, g.scal,
-                 g.ranks, g.offsets);
-}
-
 }  // namespace
+
+size_t select_workspace_bytes(int64_t cols, int64_t nslices) {
+  const int64_t ctas = std::min<int64_t>((nslices + SEL_SLICE_LANES - 1) / SEL_SLICE_LANES,
+                                         SEL_MAX_CTAS);
+  return sizeof(double) * (size_t)(cols * nslices) +
+         sizeof(double) * (size_t)(ctas * SEL_CAND) + sizeof(SelState);
+}
+
+int select_launches(bool fp64) { return 3 + (fp64 ? KeyOf<double>::ROUNDS : KeyOf<float>::ROUNDS); }
 
 template <typename T>
 cudaError_t select_segments(const SelectSeg *segs, int count, cudaStream_t st) {
@@ -317,16 +521,39 @@ cudaError_t trunc_sums(const T *sig, int cols, int nslices, int64_t k, double *s
 template cudaError_t trunc_sums<float>(const float *, int, int, int64_t, double *, cudaStream_t);
 template cudaError_t trunc_sums<double>(const double *, int, int, int64_t, double *, cudaStream_t);
 
+// ws: select_workspace_bytes(cols, nslices) bytes, 16-byte aligned: the tail sums, the
+// search round's per-CTA partial sums, the search state (zeroed here, in stream order).
 template <typename T>
-cudaError_t select_ranks(const T *sig, int cols, int nslices, double eps, void *keys_ws,
-                         double *scal, int *ranks, int64_t *offsets, cudaStream_t st) {
-  select_kernel<T><<<1, ST, 0, st>>>(sig, cols, nslices, eps, keys_ws, scal, ranks, offsets);
+cudaError_t select_ranks(const T *sig, int cols, int nslices, double eps, void *ws,
+                         double *scal, int *ranks, int64_t *offsets, int *status,
+                         cudaStream_t st) {
+  if (cols < 1 || nslices < 1) return cudaErrorInvalidValue;
+  const double eps2 = eps * eps;
+  double *tail = reinterpret_cast<double *>(ws);
+  const int ctas = (int)std::min<int64_t>(((int64_t)nslices + SEL_SLICE_LANES - 1) /
+                                              SEL_SLICE_LANES,
+                                          SEL_MAX_CTAS);
+  const int per_cta = (nslices + ctas - 1) / ctas;
+  double *part = tail + (int64_t)cols * nslices;
+  SelState *state = reinterpret_cast<SelState *>(part + (int64_t)ctas * SEL_CAND);
+  cudaError_t e = cudaMemsetAsync(state, 0, sizeof(SelState), st);
+  if (e != cudaSuccess) return e;
+  sel_tails_kernel<T><<<(nslices + SEL_WARPS - 1) / SEL_WARPS, 256, 0, st>>>(sig, cols, nslices,
+                                                                            eps2, tail, state);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int r = 0; r < KeyOf<T>::ROUNDS; ++r) {
+    sel_round_kernel<T><<<ctas, 256, 0, st>>>(sig, cols, nslices, eps2, tail, part, state,
+                                              per_cta);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  sel_finish_kernel<T><<<1, ST, 0, st>>>(sig, cols, nslices, eps2, tail, state, scal, ranks,
+                                         offsets, status);
   return cudaGetLastError();
 }
 
 template cudaError_t select_ranks<float>(const float *, int, int, double, void *, double *, int *,
-                                         int64_t *, cudaStream_t);
+                                         int64_t *, int *, cudaStream_t);
 template cudaError_t select_ranks<double>(const double *, int, int, double, void *, double *,
-                                          int *, int64_t *, cudaStream_t);
+                                          int *, int64_t *, int *, cudaStream_t);
 
 }  // namespace tsvdm

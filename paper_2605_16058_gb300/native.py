@@ -20,6 +20,8 @@ P_FP64, P_FP32, P_TF32, P_BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": P_FP64, "fp32": P_FP32, "tf32": P_TF32, "bf16x3": P_BF16X3}
 JACOBI_AUTO, JACOBI_FMA, JACOBI_TC = 0, 1, 2
 ENGINES = {"auto": JACOBI_AUTO, "fma": JACOBI_FMA, "tc": JACOBI_TC}
+ANGLE_FP64, ANGLE_FP32 = 0, 1
+ANGLES = {"fp64": ANGLE_FP64, "fp32": ANGLE_FP32}
 
 # every symbol include/tsvdm.h declares, with (restype, argtypes)
 _i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -33,6 +35,10 @@ SIGNATURES = {
     "tsvdm_plan_set_tuning": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
     "tsvdm_plan_set_engine": (_i32, [_vp, _i32]),
     "tsvdm_plan_set_warm_start": (_i32, [_vp, _i32]),
+    "tsvdm_plan_set_angle_precision": (_i32, [_vp, _i32]),
+    "tsvdm_plan_set_wait_limit": (_i32, [_vp, _i64]),
+    "tsvdm_plan_set_vectors": (_i32, [_vp, _i32]),
+    "tsvdm_probe_peak": (_i32, [_i32, _i64, _vp, _pdbl]),
     "tsvdm_data_transform": (_i32, [_vp, _vp, _vp]),
     "tsvdm_transform": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "tsvdm_fixed_rank": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pdbl]),
@@ -148,6 +154,35 @@ def tsvdm_plan_set_engine(plan, engine):
 def tsvdm_plan_set_warm_start(plan, enable):
     return check(lib().tsvdm_plan_set_warm_start(plan, int(bool(enable))),
                  "tsvdm_plan_set_warm_start")
+
+
+def tsvdm_plan_set_angle_precision(plan, angles):
+    a = ANGLES[angles] if isinstance(angles, str) else int(angles)
+    return check(lib().tsvdm_plan_set_angle_precision(plan, a), "tsvdm_plan_set_angle_precision")
+
+
+VECTORS_ACCUMULATE, VECTORS_SECOND_PASS = 0, 1
+VECTORS = {"accumulate": VECTORS_ACCUMULATE, "second_pass": VECTORS_SECOND_PASS}
+
+
+def tsvdm_plan_set_vectors(plan, mode):
+    m = VECTORS[mode] if isinstance(mode, str) else int(mode)
+    return check(lib().tsvdm_plan_set_vectors(plan, m), "tsvdm_plan_set_vectors")
+
+
+def tsvdm_plan_set_wait_limit(plan, polls):
+    return check(lib().tsvdm_plan_set_wait_limit(plan, int(polls)), "tsvdm_plan_set_wait_limit")
+
+
+PROBE_FP32_FMA, PROBE_TF32_MMA, PROBE_BF16_MMA, PROBE_FP64_FMA = 0, 1, 2, 3
+
+
+def tsvdm_probe_peak(unit, iters, stream=None):
+    """Measured TFLOP/s of one unit (see include/tsvdm.h)."""
+    out = ctypes.c_double(math.nan)
+    check(lib().tsvdm_probe_peak(int(unit), int(iters), _stream(stream), ctypes.byref(out)),
+          "tsvdm_probe_peak")
+    return out.value
 
 
 def tsvdm_data_transform(plan, X, M):

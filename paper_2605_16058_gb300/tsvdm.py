@@ -103,6 +103,19 @@ class Plan:
         """Engine of the Jacobi Gram / rotation products: "auto", "fma" or "tc"."""
         N.tsvdm_plan_set_engine(self.handle, engine)
 
+    def set_angle_precision(self, angles):
+        """Arithmetic of the slice SVDs' rotation test and angle: "fp64" (default) or "fp32"."""
+        N.tsvdm_plan_set_angle_precision(self.handle, angles)
+
+    def set_vectors(self, mode):
+        """How singular vectors are formed: "accumulate" (one pass, default) or
+        "second_pass" (singular values first, then the kept triplets' other side)."""
+        N.tsvdm_plan_set_vectors(self.handle, mode)
+
+    def set_wait_limit(self, polls):
+        """Bound (polls) of the tensor-core slice-SVD kernel's scheduler waits; 0 = default."""
+        N.tsvdm_plan_set_wait_limit(self.handle, polls)
+
     def transform(self, X, M, inverse=False, out=None):
         out = out if out is not None else torch.empty_like(X)
         N.tsvdm_transform(self.handle, X, M, int(inverse), out)

@@ -1,14 +1,20 @@
-"""Parity at the full workload sizes, in the launch configuration the benchmark times.
+"""Parity at the full workload sizes, in the launch configurations the benchmark times.
 
-  climate 1024x512x365 FP32, DCT-II, t-SVDM-II eps = 1e-2 (the benchmark workload):
+  climate 1024x512x365 FP32, DCT-II, t-SVDM-II eps = 1e-2 (the benchmark workload), with
+  the plan the benchmark runs (BF16x3 TTM, FP64 rotation angles), with the FP32 TTM, with
+  the opt-in FP32 angles, and with the two-pass vectors:
     * ranks equal Algorithm 2 applied (FP64, oracle) to the GPU's own singular values;
     * the reported error is below eps and equals sqrt(discarded / total) of those values;
-    * sampled slices: the oracle's FP64 TTM + Jacobi SVD of the slice gives the same
-      singular values (1e-5 sigma_max) and the same kept subspaces (projector 1e-4 where
-      the gap exceeds 1e-2 sigma_max).
+    * 32 slices spread over the spectrum (low-frequency slices that hold most of the energy
+      to the noise-dominated high-frequency ones): the oracle's FP64 TTM + Jacobi SVD of
+      each gives the same singular values (1e-5 sigma_max) and the same kept subspaces
+      (projector 1e-4 where the gap exceeds 1e-2 sigma_max); the oracle's singular values
+      against the threshold tau give the GPU's ranks (slices holding a sigma^2 within 1e-6
+      relative of tau excepted); the error over those slices' energy, at those ranks,
+      matches the oracle's within 1e-5.
   cfd 2048x256x512 FP32, DCT-II, t-SVDM-I k = 32 with the BF16x3 and TF32 tensor-core TTMs:
-    sampled slices against the oracle as above, and the BF16x3 relative error within 1e-5
-    of the FP32 CUDA-core path's.
+    32 sampled slices against the oracle as above, and the BF16x3 relative error within
+    1e-5 of the FP32 CUDA-core path's.
   crystal 512x256x128 FP32, DCT-II, k = 16 (learned-transform workload): loss (1e-4) and
     dL/dM (5e-3, see the test) against the full FP64 oracle.
 """
@@ -36,8 +42,13 @@ def _lib():
 
 def _sampled_slices(X, M, which):
     Ahat = oracle.ttm3(X, M, which=which)
-    U, S, V, sw = oracle.svd_slices(Ahat, threads=len(which))
+    U, S, V, sw = oracle.svd_slices(Ahat, threads=os.cpu_count())
     return U, S, V
+
+
+def _spread(n, count=32):
+    """`count` slice indices spread evenly over 0 .. n-1 (both ends included)."""
+    return sorted(set(int(round(x)) for x in np.linspace(0, n - 1, count)))
 
 
 # FP32 rotations leave errors of about u sigma_max in every column, so a subspace whose gap
@@ -52,46 +63,89 @@ def _check_slice(S_o, U_o, s_g, U_g, kk, smax, tol_sig=1e-5, tol_proj=1e-4, gap=
         assert proj_diff(U_o[:, :kk], U_g[:, :kk]) <= tol_proj
 
 
-def test_climate_tolerance_full_size():
-    from paper_2605_16058_gb300.tsvdm import Plan
-    n1, n2, n3 = 1024, 512, 365
-    eps = 1e-2
-    X = synth.climate(shape=(n1, n2, n3), seed=1)
+CLIMATE = (1024, 512, 365)
+
+
+@pytest.fixture(scope="module")
+def climate_oracle():
+    """The climate tensor, its transform, and the oracle's SVDs of 32 spread slices."""
+    n1, n2, n3 = CLIMATE
+    X = synth.climate(shape=CLIMATE, seed=1)
     M = synth.dct2_matrix(n3)
-    plan = Plan(n1, n2, n3, dtype=torch.float32)
+    which = _spread(n3)
+    U_o, S_o, _ = _sampled_slices(X.astype(np.float64),
+                                  M.astype(np.float32).astype(np.float64), which)
+    return dict(X=X, M=M, which=which, U=U_o, S=S_o)
+
+
+@pytest.mark.parametrize("prec,angles,vectors", [("bf16x3", "fp64", "accumulate"),
+                                                 ("fp32", "fp64", "accumulate"),
+                                                 ("bf16x3", "fp32", "accumulate"),
+                                                 ("bf16x3", "fp64", "second_pass")])
+def test_climate_tolerance_full_size(climate_oracle, prec, angles, vectors):
+    from paper_2605_16058_gb300.tsvdm import Plan
+    n1, n2, n3 = CLIMATE
+    eps = 1e-2
+    X, M, which = climate_oracle["X"], climate_oracle["M"], climate_oracle["which"]
+    plan = Plan(n1, n2, n3, dtype=torch.float32, prec=prec)
+    plan.set_angle_precision(angles)
+    plan.set_vectors(vectors)
     Xd, Md = t_lib(X), t_lib(M, dtype=torch.float32)
     out = plan.tolerance(Xd, Md, eps)
     ranks = out["ranks"].cpu().numpy()
     off = out["offsets"].cpu().numpy()
     assert np.array_equal(np.diff(off), ranks) and off[-1] == out["total_rank"]
-    full = plan.fixed_rank(Xd, Md, n2, rel_err=False)         # all singular values
+    # all singular values of the decomposition's first pass (the one-pass form computes the
+    # same Jacobi iterates, so Algorithm 2 on them reproduces the call's ranks)
+    plan.set_vectors("accumulate")
+    full = plan.fixed_rank(Xd, Md, n2, rel_err=False)
     S_gpu = np_lib(full["S"])
     sel = oracle.select_ranks(S_gpu, eps)
     assert np.array_equal(ranks, sel["ranks"])
     assert abs(out["rel_err"] - np.sqrt(sel["discarded"] / sel["total"])) <= 1e-12
     assert out["rel_err"] < eps
-    which = [0, 1, 182, 364]
-    Xs = X.astype(np.float64)
-    U_o, S_o, _ = _sampled_slices(Xs, M.astype(np.float32).astype(np.float64), which)
+    tau = sel["tau"]
+    U_o, S_o = climate_oracle["U"], climate_oracle["S"]
     U_pk = out["U"].cpu().double().numpy().T          # n1 x total
     smax = S_gpu.max()
+    disc_g = disc_o = tot_g = tot_o = 0.0
     for q, i in enumerate(which):
         a, b = off[i], off[i + 1]
         _check_slice(S_o[:, q], U_o[:, :, q], S_gpu[:, i], U_pk[:, a:b], b - a, smax)
+        s2 = S_o[:, q] ** 2
+        if not np.any(np.abs(s2 - tau) <= 1e-6 * tau):
+            assert ranks[i] == int(np.sum(s2 > tau)), (i, ranks[i], int(np.sum(s2 > tau)))
+        disc_o += float(np.sum(s2[ranks[i]:]))
+        tot_o += float(np.sum(s2))
+        disc_g += float(np.sum(S_gpu[ranks[i]:, i] ** 2))
+        tot_g += float(np.sum(S_gpu[:, i] ** 2))
+    assert abs(np.sqrt(disc_g / tot_g) - np.sqrt(disc_o / tot_o)) <= 1e-5
+
+
+CFD = (2048, 256, 512)
+
+
+@pytest.fixture(scope="module")
+def cfd_oracle():
+    n1, n2, n3 = CFD
+    X = synth.cfd(shape=CFD, seed=3)
+    M = synth.dct2_matrix(n3).astype(np.float32)
+    which = _spread(n3)
+    U_o, S_o, _ = _sampled_slices(X.astype(np.float64), M.astype(np.float64), which)
+    return dict(X=X, M=M, which=which, U=U_o, S=S_o)
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
-def test_cfd_fixed_rank_full_size(prec):
+def test_cfd_fixed_rank_full_size(cfd_oracle, prec):
     from paper_2605_16058_gb300.tsvdm import Plan
-    n1, n2, n3, k = 2048, 256, 512, 32
-    X = synth.cfd(shape=(n1, n2, n3), seed=3)
-    M = synth.dct2_matrix(n3).astype(np.float32)
+    n1, n2, n3 = CFD
+    k = 32
+    X, M, which = cfd_oracle["X"], cfd_oracle["M"], cfd_oracle["which"]
     Xd, Md = t_lib(X), t_lib(M)
     plan = Plan(n1, n2, n3, dtype=torch.float32, prec=prec)
     out = plan.fixed_rank(Xd, Md, k)
     S_g, U_g = np_lib(out["S"]), np_lib(out["U"])
-    which = [0, 7, 255, 511]
-    U_o, S_o, _ = _sampled_slices(X.astype(np.float64), M.astype(np.float64), which)
+    U_o, S_o = cfd_oracle["U"], cfd_oracle["S"]
     # TF32 products carry ~2^-11 relative error, BF16x3 ~2^-16 (error model of the TTM)
     tol = 1e-5 if prec == "bf16x3" else 2e-3
     smax = S_g.max()

@@ -115,3 +115,35 @@ def test_noalloc_selection_matches_algorithm2_on_exact_spectra(eps):
             assert tau == want["tau"]
         else:
             assert tau == -1.0
+
+
+def test_noalloc_invalid_values_are_reported_and_minus_zero_is_zero():
+    """-0 is a zero singular value (same result as +0); a NaN, an infinity or a negative
+    value makes the call report NaN in the summary with every rank and offset 0; the next
+    call on valid values is unaffected."""
+    from paper_2605_16058_gb300 import native
+    S = np.array([[4.0, 3.0], [2.0, 1.0], [1.0, 0.0], [0.0, 0.0]])
+    cols, ns = S.shape
+
+    def run(Sm, eps=0.3):
+        sig = torch.tensor(np.ascontiguousarray(Sm.T).astype(np.float32), device="cuda")
+        ranks = torch.full((ns,), -1, dtype=torch.int32, device="cuda")
+        offs = torch.full((ns + 1,), -1, dtype=torch.int64, device="cuda")
+        summ = torch.zeros(4, dtype=torch.float64, device="cuda")
+        assert _noalloc(sig, cols, ns, eps, ranks, offs, summ) == native.OK
+        torch.cuda.synchronize()
+        return ranks.cpu().numpy(), offs.cpu().numpy(), summ.cpu().numpy()
+
+    r0, o0, s0 = run(S)
+    Sm = S.copy()
+    Sm[3, 0] = -0.0
+    Sm[2, 1] = -0.0
+    r1, o1, s1 = run(Sm)
+    assert np.array_equal(r0, r1) and np.array_equal(o0, o1) and np.array_equal(s0, s1)
+    for bad in (np.nan, np.inf, -1.0):
+        Sb = S.copy()
+        Sb[2, 1] = bad
+        rb, ob, sb = run(Sb)
+        assert np.all(np.isnan(sb)) and not rb.any() and not ob.any(), bad
+    r2, o2, s2 = run(S)
+    assert np.array_equal(r0, r2) and np.array_equal(o0, o2) and np.array_equal(s0, s2)
