@@ -73,8 +73,9 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--angles", default="fp64", choices=["fp64", "fp32"],
                     help="arithmetic of the slice SVDs' rotation test and angle")
-    ap.add_argument("--vectors", default="accumulate", choices=["accumulate", "second_pass"],
-                    help="singular vectors in one pass, or kept ones in a second pass")
+    ap.add_argument("--vectors", default="second_pass", choices=["accumulate", "second_pass"],
+                    help="singular vectors in one pass, or the kept ones in a second pass "
+                         "(Sec. 3.4's compute-efficient strategy, the default here)")
     ap.add_argument("--quick", action="store_true",
                     help="skip the other configurations (all-FP64 GPU path, CFD, batch, "
                          "the 64x48x16 FP64 case)")
@@ -713,6 +714,23 @@ def main():
     value = world * in_bytes / (ms_step * 1e-3) / 1e9
     slices_s = world * n3 / (ms_step * 1e-3)
 
+    # the other vector strategy on the same plan and input (one timed call after one warm-up)
+    other = "accumulate" if args.vectors == "second_pass" else "second_pass"
+    alt = None
+    if len(shape) == 3 and not args.quick:
+        plan.set_vectors(other)
+        step()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        tot_a, rel_a, _ = step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        alt = {"vectors": other, "ms_per_step": a0.elapsed_time(a1), "rel_err": rel_a,
+               "total_rank": int(tot_a)}
+        plan.set_vectors(args.vectors)
+        step()
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -812,6 +830,7 @@ def main():
                          "unit": "GB/s", "frac": ttm_gbs / pk["hbm_gbs"],
                          "peak_source": "of %s" % src},
         "gpu_launches": int(launches),
+        "vectors": args.vectors, "angles": args.angles, "other_vectors": alt,
         "clocks": clocks,
         "e2e": e2e,
         "data_driven_m": data_m,

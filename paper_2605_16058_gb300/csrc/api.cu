@@ -386,7 +386,7 @@ tsvdm_status second_pass(tsvdm_plan_s *p, int64_t k, const int *ranks, const int
   jp.sweeps = p->tp_sweeps;
   jp.rots = p->rots;
   jp.norm2 = nullptr;
-  jp.inner_sweeps = p->inner_sweeps;
+  jp.inner_sweeps = 1;      // Z's columns are nearly orthogonal: one Gram sweep per block pair
   jp.desc = p->tp_desc;
   jp.engine = (sizeof(T) == 4 && p->engine != JACOBI_FMA) ? JACOBI_TC : JACOBI_FMA;
   jp.sched = p->sched;

@@ -380,33 +380,30 @@ __device__ __forceinline__ void angle64(double a, double b, double g, double &c,
   db = fma(t, g, b);
 }
 
-// The FP64 rotation of an FP32 slice's pair, with few FP64 operations (the FP64 rate of the
-// GPU is a small fraction of its FP32 rate): FP32 estimates of t and c refined by one
-// Newton step each in FP64 arithmetic.  t solves g2 t^2 + 2 h t - g2 = 0 (the quadratic of
-// tan theta: t^2 + 2 zeta t - 1 = 0 times g2), whose derivative 2 (g2 t + h) has magnitude
-// 2 sqrt(h^2 + g2^2) at the root; from an estimate with absolute error d (|t| <= 1) the
-// step leaves an error of about d^2 / 2 plus the FP64 rounding of f(t0), so ~1e-13 from an
-// FP32 estimate.  c = (1 + t^2)^(-1/2) takes the Newton step c + c (1 - (1 + t^2) c^2) / 2
-// of the reciprocal square root.  s = c t and the rotated diagonal a - t g, b + t g follow
-// in FP64; the caller rounds the results to FP32.
-__device__ __forceinline__ void angle64_f32(float a, float b, float g, double &c, double &sn,
-                                            double &da, double &db) {
+// The FP64 rotation angle of an FP32 slice's pair, with few FP64 operations (the FP64 rate
+// of the GPU is a small fraction of its FP32 rate).  The angle t = tan(theta) solves
+// g2 t^2 + 2 h t - g2 = 0 (t^2 + 2 zeta t - 1 = 0 times g2; h = b - a, g2 = 2 g), whose
+// derivative 2 (g2 t + h) has magnitude 2 sqrt(h^2 + g2^2) at the root: from the FP32
+// estimate t0 (absolute error d, |t| <= 1) one Newton step in FP64 arithmetic leaves about
+// d^2 / 2 plus the FP64 rounding of f(t0), ~1e-13.  The rotation then takes that angle in
+// the slice's precision: c = 1 / sqrt(1 + t^2), s = c t and the rotated diagonal a - t g,
+// b + t g from t rounded to FP32 (the values the FP32 rotation is applied with).
+__device__ __forceinline__ void angle64_f32(float a, float b, float g, float &c, float &sn,
+                                            float &da, float &db) {
   const float hf = b - a, g2f = 2.f * g;
   float t0 = fabsf(g2f) / (fabsf(hf) + hypotf(hf, g2f));
   if ((hf >= 0.f) != (g2f >= 0.f)) t0 = -t0;
-  const double ad = a, bd = b, gd = g, g2 = 2.0 * gd, h = bd - ad, td = t0;
-  const double f = fma(g2, td * td, fma(2.0 * h, td, -g2));      // g2 t^2 + 2 h t - g2
+  const double gd = g, g2 = gd + gd, h = (double)b - (double)a, td = t0;
+  const double f = fma(g2, td * td, fma(h, (double)(2.f * t0), -g2));   // g2 t^2 + 2 h t - g2
   const float fp = 2.f * fmaf(g2f, t0, hf);                      // f'(t0), FP32 suffices
   const float rf = __frcp_rn(fp);     // |f'| >= 2 |g2| > 0; infinite only for denormal pairs
-  const double t = isfinite(rf) ? fma(-f, (double)rf, td) : td;
-  const double u = fma(t, t, 1.0);
-  const float c0f = __frsqrt_rn((float)u);
-  const double c0 = c0f;
-  const double e = fma(-u, c0 * c0, 1.0);
-  c = fma((double)(0.5f * c0f), e, c0);
+  const float t = isfinite(rf) ? (float)fma(-f, (double)rf, td) : t0;
+  // correctly rounded 1/sqrt: an approximate reciprocal square root biased c (and the
+  // column norms, over thousands of rotations) by ~1e-5
+  c = __frsqrt_rn(fmaf(t, t, 1.f));
   sn = c * t;
-  da = fma(-t, gd, ad);
-  db = fma(t, gd, bd);
+  da = fmaf(-t, g, a);
+  db = fmaf(t, g, b);
 }
 
 // The same rotation in FP32 (the opt-in FP32 angle mode).  c is the correctly rounded
@@ -425,8 +422,8 @@ __device__ __forceinline__ void angle32(float a, float b, float g, float &c, flo
 
 // Rotation of one pair from its current Gram entries (a = g_ii, b = g_jj, g = g_ij),
 // stored in slot `sl` as pair k.  The test and the angle run in FP64 (from the FP32 Gram
-// entries of an FP32 slice, the results rounded to FP32), or in FP32 when a32 is set for
-// an FP32 slice.
+// entries of an FP32 slice, whose rotation then takes the angle rounded to FP32), or in
+// FP32 when a32 is set for an FP32 slice.
 template <typename T, int W2, int NS, typename SM>
 __device__ __forceinline__ void pair_angle(SM &s, int sl, int k, int i, int j, T a, T b, T g,
                                            double tol, double tol2, bool a32) {
@@ -451,15 +448,21 @@ __device__ __forceinline__ void pair_angle(SM &s, int sl, int k, int i, int j, T
       }
     }
     if (!done) {
-      double c, sn, da, db;
-      if constexpr (sizeof(T) == 4)
+      if constexpr (sizeof(T) == 4) {
+        float c, sn, da, db;
         angle64_f32(a, b, g, c, sn, da, db);
-      else
+        s.cs[sl][2 * k] = c;
+        s.cs[sl][2 * k + 1] = sn;
+        s.dd[sl][2 * k] = da;
+        s.dd[sl][2 * k + 1] = db;
+      } else {
+        double c, sn, da, db;
         angle64(a, b, g, c, sn, da, db);
-      s.cs[sl][2 * k] = (T)c;
-      s.cs[sl][2 * k + 1] = (T)sn;
-      s.dd[sl][2 * k] = (T)da;
-      s.dd[sl][2 * k + 1] = (T)db;
+        s.cs[sl][2 * k] = (T)c;
+        s.cs[sl][2 * k + 1] = (T)sn;
+        s.dd[sl][2 * k] = (T)da;
+        s.dd[sl][2 * k + 1] = (T)db;
+      }
     }
     rot = 1;
     s.any_rot = 1;
@@ -1012,16 +1015,10 @@ __device__ __forceinline__ void cross_angle(SmemTc &s, int sl, int k, float a, f
     s.nonfinite = 1;
   } else if (a32 ? rot_test_f32(a, b, g, tol, tol2) : decide64(a, b, g, tol2d)) {
     float da, db;
-    if (a32) {
+    if (a32)
       angle32(a, b, g, c, sn, da, db);
-    } else {
-      double cd, sd, dad, dbd;
-      angle64_f32(a, b, g, cd, sd, dad, dbd);
-      c = (float)cd;
-      sn = (float)sd;
-      da = (float)dad;
-      db = (float)dbd;
-    }
+    else
+      angle64_f32(a, b, g, c, sn, da, db);
     s.dd[sl][2 * k] = da;
     s.dd[sl][2 * k + 1] = db;
     rot = 1;
@@ -1096,7 +1093,8 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
   constexpr int NOWN = NB - NP;            // blocks of the update threads
   // work split per step (the cost of a block is about three Q items): warps 0..4 take two
   // blocks and three Q items, warps 5 and 6 two or three blocks and no Q item, the angle
-  // warp its hand-over block, the rotations and one Q item
+  // warp its hand-over block, the rotations and one Q item (with FP64 angles, whose
+  // arithmetic lengthens the angle warp's step, warp 5 takes that Q item)
   constexpr int QW = 5 * 32;               // update threads that rotate Q
   constexpr int XT = 5 * 32;               // first update thread with a third block
   static_assert(2 * NU + (NOWN - 2 * NU) == NOWN && NOWN - 2 * NU <= NU - XT, "block split");
@@ -1199,9 +1197,11 @@ __device__ void inner_sweep_cross(SmemTc &s, double tol, bool first, int tid,
       }
       if (tid < QW)
         for (int u = 0; u < 3; ++u) cross_q_item(s, cs2, tid + u * QW, step);
+      else if (!a32 && tid < QW + 32)   // FP64 angles: warp 5 takes the angle warp's Q item
+        cross_q_item(s, cs2, 3 * QW + (tid - QW), step);
     }
-    if (warp == AW) cross_q_item(s, reinterpret_cast<const float2 *>(s.cs[sl]), 3 * QW + lane,
-                                 step);
+    if (warp == AW && a32)
+      cross_q_item(s, reinterpret_cast<const float2 *>(s.cs[sl]), 3 * QW + lane, step);
     bar.sync();
   }
 }

@@ -9,7 +9,8 @@
 // six products of order >= 2^-24 are accumulated, so the result has FP32-level accuracy.
 // One persistent CTA per SM (a kernel holding tensor memory runs one CTA per SM) takes
 // output tiles (slice, a-tile, b-tile); 512 threads convert (four per row of A, two per
-// row of B), one issues the MMAs, all drain TMEM.  Stages are double-buffered; every wait is bounded.
+// row of B; the next K-block's values are loaded while the current one's MMAs run), one
+// issues the MMAs, all drain TMEM.  Stages are double-buffered; every wait is bounded.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -69,73 +70,73 @@ __global__ void __launch_bounds__(RT, 1)
     const int64_t c0 = offsets ? offsets[slice] : slice * k;
     const int64_t cnt = offsets ? offsets[slice + 1] - c0 : k;
     const int nkb = (int)((cnt + RK - 1) / RK);
-    for (int kb = 0; kb < nkb; ++kb) {
+    // operand values of K-block kb: A row a0 + (tid & 127), 8 columns of chunk tid >> 7;
+    // B row b0 + (tid & 255), 16 columns of half tid >> 8
+    const int ra = tid & 127, cha = tid >> 7;
+    const int64_t arow = a0 + ra;
+    const int64_t bb = b0 + (tid & 255);
+    const int bh = tid >> 8;
+    auto load_blk = [&](int kb, float (&xa)[8], float (&xb)[16]) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int64_t c = (int64_t)kb * RK + cha * 8 + e;
+        xa[e] = (arow < n1 && c < cnt)
+                    ? __ldg(U + (c0 + c) * n1 + arow) * (S ? __ldg(S + c0 + c) : 1.f)
+                    : 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int64_t c = (int64_t)kb * RK + bh * 16 + e;
+        // V(b, c) at (c0 + c) n2 + b, or (vtrans, uniform k) at c0 n2 + b k + c
+        xb[e] = (bb < n2 && c < cnt)
+                    ? __ldg(vtrans ? V + c0 * n2 + bb * k + c : V + (c0 + c) * n2 + bb)
+                    : 0.f;
+      }
+    };
+    // one K-block: the operands already in registers go to stage kb & 1 as three BF16
+    // terms, the next block's values are loaded while this one's MMAs run
+    auto run_blk = [&](int kb, float (&xa)[8], float (&xb)[16], float (&na)[8],
+                       float (&nb)[16]) {
       const int b = kb & 1;
       if (kb >= 2) wait(b);                        // the MMAs of K-block kb-2 read stage b
       unsigned char *st = s.st[b];
-      // A: thread -> row a0 + (tid & 127), the 8 columns c of chunk tid >> 7
       {
-        const int r = tid & 127, ch = tid >> 7;
-        const int64_t a = a0 + r;
-        {
-          uint32_t w[3][4];
+        uint32_t w[3][4];
 #pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            float x[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int64_t c = (int64_t)kb * RK + ch * 8 + e + u;
-              x[u] = (a < n1 && c < cnt)
-                         ? __ldg(U + (c0 + c) * n1 + a) * (S ? __ldg(S + c0 + c) : 1.f)
-                         : 0.f;
-            }
-            __nv_bfloat16 p0, p1, p2, q0, q1, q2;
-            tc::split3(x[0], p0, p1, p2);
-            tc::split3(x[1], q0, q1, q2);
-            w[0][e / 2] = tc::pack2(p0, q0);
-            w[1][e / 2] = tc::pack2(p1, q1);
-            w[2][e / 2] = tc::pack2(p2, q2);
-          }
-          const uint32_t off = tc::sw64((uint32_t)r, (uint32_t)ch);
-#pragma unroll
-          for (int u = 0; u < 3; ++u)
-            *reinterpret_cast<uint4 *>(st + u * A_TERM + off) =
-                make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
+        for (int e = 0; e < 8; e += 2) {
+          __nv_bfloat16 p0, p1, p2, q0, q1, q2;
+          tc::split3(xa[e], p0, p1, p2);
+          tc::split3(xa[e + 1], q0, q1, q2);
+          w[0][e / 2] = tc::pack2(p0, q0);
+          w[1][e / 2] = tc::pack2(p1, q1);
+          w[2][e / 2] = tc::pack2(p2, q2);
         }
+        const uint32_t off = tc::sw64((uint32_t)ra, (uint32_t)cha);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          *reinterpret_cast<uint4 *>(st + u * A_TERM + off) =
+              make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
       }
-      // B: thread -> row b0 + (tid & 255) (one column of the output), the 16 columns c of
-      // half tid >> 8
-      {
-        const int64_t bb = b0 + (tid & 255);
-        const int bh = tid >> 8;
 #pragma unroll
-        for (int ch = bh * 2; ch < bh * 2 + 2; ++ch) {
-          uint32_t w[3][4];
+      for (int h = 0; h < 2; ++h) {
+        const int ch = bh * 2 + h;
+        uint32_t w[3][4];
 #pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            float x[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int64_t c = (int64_t)kb * RK + ch * 8 + e + u;
-              // V(b, c) at (c0 + c) n2 + b, or (vtrans, uniform k) at c0 n2 + b k + c
-              x[u] = (bb < n2 && c < cnt)
-                         ? __ldg(vtrans ? V + c0 * n2 + bb * k + c : V + (c0 + c) * n2 + bb)
-                         : 0.f;
-            }
-            __nv_bfloat16 p0, p1, p2, q0, q1, q2;
-            tc::split3(x[0], p0, p1, p2);
-            tc::split3(x[1], q0, q1, q2);
-            w[0][e / 2] = tc::pack2(p0, q0);
-            w[1][e / 2] = tc::pack2(p1, q1);
-            w[2][e / 2] = tc::pack2(p2, q2);
-          }
-          const uint32_t off = tc::sw64((uint32_t)(tid & 255), (uint32_t)ch);
-#pragma unroll
-          for (int u = 0; u < 3; ++u)
-            *reinterpret_cast<uint4 *>(st + 3 * A_TERM + u * B_TERM + off) =
-                make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
+        for (int e = 0; e < 8; e += 2) {
+          __nv_bfloat16 p0, p1, p2, q0, q1, q2;
+          tc::split3(xb[h * 8 + e], p0, p1, p2);
+          tc::split3(xb[h * 8 + e + 1], q0, q1, q2);
+          w[0][e / 2] = tc::pack2(p0, q0);
+          w[1][e / 2] = tc::pack2(p1, q1);
+          w[2][e / 2] = tc::pack2(p2, q2);
         }
+        const uint32_t off = tc::sw64((uint32_t)(tid & 255), (uint32_t)ch);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          *reinterpret_cast<uint4 *>(st + 3 * A_TERM + u * B_TERM + off) =
+              make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
       }
+      if (kb + 1 < nkb) load_blk(kb + 1, na, nb);
       tc::fence_proxy_async();
       tc::fence_before_sync();
       __syncthreads();
@@ -151,6 +152,12 @@ __global__ void __launch_bounds__(RT, 1)
           }
         tc::mma_commit(&s.bar[b]);
       }
+    };
+    float xa0[8], xb0[16], xa1[8], xb1[16];
+    if (nkb > 0) load_blk(0, xa0, xb0);
+    for (int kb = 0; kb < nkb; kb += 2) {
+      run_blk(kb, xa0, xb0, xa1, xb1);
+      if (kb + 1 < nkb) run_blk(kb + 1, xa1, xb1, xa0, xb0);
     }
     for (int kb = nkb >= 2 ? nkb - 2 : 0; kb < nkb; ++kb) wait(kb & 1);
     tc::fence_after_sync();
@@ -175,7 +182,7 @@ __global__ void __launch_bounds__(RT, 1)
             if (bcol < n2) {
               const float v = subtract ? O[a + n1 * bcol] - d[e] : d[e];
               O[a + n1 * bcol] = v;
-              ss += (double)v * (double)v;
+              if (sumsq) ss += (double)v * (double)v;   // FP64 only when it is asked for
             }
           }
         }

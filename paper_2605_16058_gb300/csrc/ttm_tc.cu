@@ -12,17 +12,24 @@
 //
 // Persistent: one CTA per SM (a kernel that holds tensor memory runs one CTA per SM)
 // loops over row tiles; the stage ring runs across tiles.  Warp roles (512 threads):
-//   warp 0       TMA producer: raw FP32 X tile (128 rows x 32 t, no swizzle) and the
-//                pre-converted K-major B tiles (swizzled) of each stage;
+//   warp 0       TMA producer: the pre-converted K-major B tiles (swizzled) of each stage;
 //   warp 1       TMEM allocation; one thread issues the MMAs and commits them (a tile's
 //                first MMA waits until the epilogue has read the previous accumulator);
-//   warps 4..11  converters (two threads per row, 16 t each): FP32 X -> K-major swizzled
-//                operand tiles;
-//   warps 12..15 epilogue (tcgen05.ld of its own TMEM lane -> scale -> store), which
-//                overlaps the next tile's loads and conversions.
+//   warps 4..11  converters (two threads per row, 16 t each): FP32 X, loaded from global
+//                memory straight into registers two k-steps ahead (a warp's 32 rows are
+//                128 contiguous bytes for each t), -> K-major swizzled operand tiles, so a
+//                stage holds only the operands (three stages fit where the raw X tile left
+//                room for two);
+//   warps 12..15 epilogue (tcgen05.ld of its own TMEM lane -> scale -> a shared-memory
+//                staging buffer of 32 columns -> one TMA bulk tensor store per 128 x 32
+//                box, two buffers alternating; per-element stores when a beta Z term is
+//                added), which overlaps the next tile's loads and conversions.  (Scalar
+//                stores of 384 columns per row took longer than the tile's MMAs, and a
+//                tile's MMAs wait for the epilogue to have read the single accumulator.)
 // Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT in the status
 // word, every role leaves its loop and TMEM is released.  Nothing traps.
 #include <cuda.h>
+#include <string.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -34,7 +41,9 @@ namespace {
 
 constexpr int TBM = 128;
 constexpr int TBK = 32;
-constexpr int MAX_STAGES = 4;
+constexpr int MAX_STAGES = 6;
+constexpr uint32_t EPI_COLS = 32;                 // columns per epilogue TMA store
+constexpr uint32_t EPI_BUF = TBM * EPI_COLS * 4;  // one staging buffer (16 KB)
 constexpr int TC_THREADS = 512;   // warps 0 TMA, 1 MMA + TMEM, 4-11 converters, 12-15 epilogue
 constexpr unsigned SPIN_LIMIT = 1u << 26;
 
@@ -45,7 +54,9 @@ struct TcParams {
   int box_rows;      // rows of one B tensor-map box (divides nsub, <= 256)
   int stages;        // pipeline depth (2..MAX_STAGES)
   int kt_count;      // ceil(n / TBK)
+  int tma_store;     // 1: the epilogue writes Y through shared memory with TMA stores
   int prec;          // TSVDM_P_BF16X3 or TSVDM_P_TF32
+  const float *X;
   float *Y;
   const float *Z;
   const double *scale_ptr, *beta_ptr;
@@ -88,24 +99,23 @@ struct TcLayout {
 
 __host__ __device__ inline TcLayout tc_layout(int npad, int prec, int stages) {
   TcLayout L;
-  const uint32_t raw = TBK * TBM * 4;                       // 16 KB
   const uint32_t a = (prec == TSVDM_P_BF16X3) ? 2u * TBM * 64 : TBM * 128u;   // 16 KB
   const uint32_t b = (prec == TSVDM_P_BF16X3) ? 2u * npad * 64 : npad * 128u;
   L.a_bytes = a;
   L.b_bytes = b;
   L.raw = 0;
-  L.a = raw;
-  L.b = raw + a;
-  uint32_t st = raw + a + b;
+  L.a = 0;
+  L.b = a;
+  uint32_t st = a + b;
   st = (st + 1023) & ~1023u;
   L.stage = st;
-  L.total = stages * st + 1024;                            // + barriers / TMEM address
+  L.total = stages * st + 1024 + 2 * EPI_BUF;              // + barriers, epilogue buffers
   return L;
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    ttm_tc_kernel(const __grid_constant__ CUtensorMap mapX,
-                  const __grid_constant__ CUtensorMap mapB, TcParams p) {
+    ttm_tc_kernel(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapY,
+                  TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // align the dynamic shared memory base to 1024 bytes
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -117,6 +127,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t *tfull = empty + MAX_STAGES;        // a tile's accumulator is complete
   uint64_t *tempty = tfull + 1;                // the epilogue has read it (TMEM free)
   uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
+  float *ebuf = (float *)(smem + STAGES * L.stage + 1024);     // 2 x [32 cols][128 rows]
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -161,20 +172,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // tiles (iteration it = tiles before x nk + kt), so the TMA and the converters fill the
   // next tile's stages while the epilogue warps drain the accumulator of the last one.
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer: raw FP32 X tile + pre-split K-major B tiles
-    const uint32_t bytes = TBK * TBM * 4 + L.b_bytes;
+    // ---------------- TMA producer: pre-split K-major B tiles
+    const uint32_t bytes = L.b_bytes;
     const int ops = bf ? 2 : 1;
     const uint32_t row_bytes = bf ? 64 : 128;
     int it = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int m0 = tile * TBM;
       for (int kt = 0; kt < nk; ++kt, ++it) {
         const int s = it % STAGES, u = it / STAGES;
         if (u > 0 && !wait(&empty[s], (u - 1) & 1)) { ok = false; break; }
         unsigned char *st = smem + s * L.stage;
         mbar_expect_tx(&full[s], bytes);
-        tma_load_2d(st + L.raw, &mapX, &full[s], m0, kt * TBK);
         for (int o = 0; o < ops; ++o)
           for (int r0 = 0; r0 < p.nsub; r0 += p.box_rows)
             tma_load_2d(st + L.b + (uint32_t)o * p.nsub * row_bytes + (uint32_t)r0 * row_bytes,
@@ -231,18 +240,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int row = (tid - 128) & 127, kh = (tid - 128) >> 7;
     double ss = 0.0;
     const bool do_ss = p.sumsq != nullptr;
+    constexpr int KH = TBK / 2;
+    // X(grow, t) for this thread's row and its 16 t of k-step kt (zero past P or n)
+    auto load_x = [&](int tile, int kt, float (&x)[KH]) {
+      const int64_t grow = (int64_t)tile * TBM + row;
+      const bool rin = tile < ntiles && grow < p.P;
+#pragma unroll
+      for (int k = 0; k < KH; ++k) {
+        const int64_t t = (int64_t)kt * TBK + kh * KH + k;
+        x[k] = (rin && t < p.n) ? __ldg(p.X + grow + p.P * t) : 0.f;
+      }
+    };
+    // the k-steps of this CTA in order: (tile, kt), tiles blockIdx.x, + gridDim.x, ...
+    auto advance = [&](int &tile, int &kt) {
+      if (++kt == nk) {
+        kt = 0;
+        tile += gridDim.x;
+      }
+    };
+    float x[KH], xn1[KH], xn2[KH];
+    int t1 = blockIdx.x, k1 = 0;
+    load_x(t1, k1, x);
+    advance(t1, k1);
+    load_x(t1, k1, xn1);
+    advance(t1, k1);
     int it = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       for (int kt = 0; kt < nk; ++kt, ++it) {
         const int s = it % STAGES, u = it / STAGES;
+        load_x(t1, k1, xn2);                       // two k-steps ahead
+        advance(t1, k1);
         if (!wait(&full[s], u & 1)) { ok = false; break; }
         unsigned char *st = smem + s * L.stage;
-        const float *raw = (const float *)(st + L.raw);
-        constexpr int KH = TBK / 2;
-        float x[KH];
-#pragma unroll
-        for (int k = 0; k < KH; ++k) x[k] = raw[(kh * KH + k) * TBM + row];
         if (do_ss) {
 #pragma unroll
           for (int k = 0; k < KH; ++k) ss += (double)x[k] * (double)x[k];
@@ -281,6 +311,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&conv[s]);
+#pragma unroll
+        for (int k = 0; k < KH; ++k) {
+          x[k] = xn1[k];
+          xn1[k] = xn2[k];
+        }
       }
     }
     if (do_ss) {
@@ -291,6 +326,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp >= 12) {
     // ---------------- epilogue (thread = TMEM lane = row): scale, optional beta Z, store
     const int row = tid - 384;
+    int echunk = 0;                      // staging chunks so far (over all tiles)
     const uint32_t lane_base = (uint32_t)(32 * (warp - 12)) << 16;
     const float scale = p.scale_ptr ? (float)(*p.scale_ptr) : 1.f;
     const float beta = p.beta_ptr ? (float)(*p.beta_ptr) : 0.f;
@@ -299,21 +335,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!wait(tfull, j & 1)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int64_t grow = (int64_t)tile * TBM + row;
-      for (int j0 = 0; j0 < p.nsub; j0 += 16) {
-        uint32_t v[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-            "%11, %12, %13, %14, %15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(tmem + lane_base + (uint32_t)j0));
+      if (p.tma_store) {
+        // 32 columns at a time: TMEM -> staging buffer (column-major [32][128], conflict
+        // free) -> one TMA store of the 128 x 32 box; two buffers alternate, and a buffer
+        // is rewritten only after the store issued from it two chunks before has read it
+        for (int c = 0; c * (int)EPI_COLS < p.nsub; ++c, ++echunk) {
+          float *buf = ebuf + (echunk & 1) * (EPI_BUF / 4);
+          if (row == 0 && echunk >= 2)
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          uint32_t v[32];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+              "%10, %11, %12, %13, %14, %15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(tmem + lane_base + (uint32_t)(c * EPI_COLS)));
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+              "%10, %11, %12, %13, %14, %15}, [%16];"
+              : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(tmem + lane_base + (uint32_t)(c * EPI_COLS + 16)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int e = 0; e < 32; ++e) buf[e * TBM + row] = scale * __uint_as_float(v[e]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          if (row == 0) {
+            asm volatile(
+                "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                    (uint64_t)&mapY),
+                "r"((int)(tile * TBM)), "r"((int)(n_base + c * EPI_COLS)), "r"(smem_u32(buf))
+                : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+        }
+      } else {
+      // 64 columns per TMEM round trip: four loads, one wait
+      for (int j0 = 0; j0 < p.nsub; j0 += 64) {
+        uint32_t v[64];
+        const int nq = (p.nsub - j0) >= 64 ? 4 : (p.nsub - j0) / 16;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (q < nq)
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                "%10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(v[16 * q + 0]), "=r"(v[16 * q + 1]), "=r"(v[16 * q + 2]), "=r"(v[16 * q + 3]),
+                  "=r"(v[16 * q + 4]), "=r"(v[16 * q + 5]), "=r"(v[16 * q + 6]), "=r"(v[16 * q + 7]),
+                  "=r"(v[16 * q + 8]), "=r"(v[16 * q + 9]), "=r"(v[16 * q + 10]), "=r"(v[16 * q + 11]),
+                  "=r"(v[16 * q + 12]), "=r"(v[16 * q + 13]), "=r"(v[16 * q + 14]), "=r"(v[16 * q + 15])
+                : "r"(tmem + lane_base + (uint32_t)(j0 + 16 * q)));
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (grow < p.P) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
+          for (int e = 0; e < 64; ++e) {
             const int64_t col = n_base + j0 + e;
-            if (col < p.J) {
+            if (e < 16 * nq && col < p.J) {
               float y = scale * __uint_as_float(v[e]);
               if (p.Z) y = fmaf(beta, p.Z[grow + p.P * col], y);
               p.Y[grow + p.P * col] = y;
@@ -321,10 +403,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
+      }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(tempty);
     }
   }
+  // the thread that issued the epilogue's TMA stores waits for them before the CTA ends
+  if (warp >= 12 && tid == 384 && p.tma_store)
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
@@ -411,15 +497,19 @@ cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t
     if (e != cudaSuccess) return e;
   }
   auto enc = get_encode();
-  CUtensorMap mapX, mapB;
-  {
-    cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)n};
+  CUtensorMap mapB, mapY;
+  // the epilogue stores Y (P x J, column-major) with TMA when Y is 16-byte aligned and no
+  // beta Z term is added (the backward's dX keeps the per-element stores)
+  const bool tma_store = Z == nullptr && ((uintptr_t)Y & 15) == 0;
+  memset(&mapY, 0, sizeof(mapY));
+  if (tma_store) {
+    cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)J};
     cuuint64_t strides[1] = {(cuuint64_t)P * 4};
-    cuuint32_t box[2] = {TBM, TBK};
+    cuuint32_t box[2] = {TBM, EPI_COLS};
     cuuint32_t es[2] = {1, 1};
-    if (enc(&mapX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)X, dims, strides, box, es,
+    if (enc(&mapY, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)Y, dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
   {
@@ -444,6 +534,8 @@ cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t
   p.box_rows = box_rows;
   p.kt_count = kpad / TBK;
   p.prec = prec;
+  p.tma_store = tma_store ? 1 : 0;
+  p.X = X;
   p.Y = Y;
   p.Z = Z;
   p.scale_ptr = scale_ptr;
@@ -469,8 +561,9 @@ cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t
     return e;
   const int64_t ntiles = (P + TBM - 1) / TBM;
   const dim3 grid((unsigned)(ntiles < sms ? ntiles : sms), (unsigned)nsplit);
-  ttm_tc_kernel<<<grid, TC_THREADS, smem, st>>>(mapX, mapB, p);
+  ttm_tc_kernel<<<grid, TC_THREADS, smem, st>>>(mapB, mapY, p);
   return cudaGetLastError();
 }
 
 }  // namespace tsvdm
+
