@@ -858,10 +858,23 @@ def main():
             tr = CayleyTrainer(Xcd, M0, cs, 16, lr=1e-3, warm_start=warm)
             runs[warm] = tr.train(50)
         (lc, ms_c), (lw, ms_w) = runs[False], runs[True]
+        split = tr.part_split(5)
+        # compressibility at a matched tolerance: t-SVDM-II of the crystal tensor with the
+        # learned transform and with DCT-II (the starting point), eps = 1e-2
+        Ml = tr.current_transform()
+        pc = Plan(*cs, dtype=torch.float32, prec=args.prec, orthogonal=True)
+        crs = {}
+        for name, Mx in (("learned", Ml), ("dct2", M0)):
+            oc = pc.tolerance(Xcd, Mx, 1e-2)
+            crs[name] = {"total_rank": int(oc["total_rank"]), "rel_err": oc["rel_err"],
+                         "compression_ratio": cs[0] * cs[1] * cs[2] /
+                         max(int(oc["total_rank"]) * (cs[0] + cs[1] + 1), 1)}
+        pc.close()
         line["learned_m"] = {"workload": "crystal-shaped 512x256x128 FP32, Cayley(DCT-II), "
                                          "k=16, 50 Adam steps lr=1e-3; slice SVDs warm-started "
                                          "from the previous step's right vectors",
-                             "fwd_bwd_ms_per_step": ms_w, "loss_first": lw[0],
+                             "fwd_bwd_ms_per_step": ms_w, "step_split_ms": split,
+                             "tsvdm2_eps_1e-2": crs, "loss_first": lw[0],
                              "loss_last": lw[-1], "cold_start_ms_per_step": ms_c,
                              "cold_start_loss_last": lc[-1]}
     line["peaks_measured"] = dict(

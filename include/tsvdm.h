@@ -22,6 +22,11 @@
  *            accept HOST pointers (pageable or pinned; detected per pointer): inputs
  *            are copied in and outputs copied out on the plan's stream, through
  *            staging buffers the plan allocates on the first such call and keeps.
+ *            Calls that allocate device memory after plan creation (each once per
+ *            plan, kept until tsvdm_plan_destroy): the first host-pointer call (staging),
+ *            tsvdm_data_transform (its one-slice plan), tsvdm_plan_set_warm_start (enable)
+ *            and tsvdm_plan_set_vectors (SECOND_PASS); tsvdm_probe_peak allocates and frees
+ *            a status word.  Every other call allocates nothing.
  *   Streams  work is enqueued on the plan's stream.  Calls return once the work is
  *            enqueued, except where a host output (rel_err, total_rank, loss) is
  *            requested: those calls synchronise the stream before returning.

@@ -55,19 +55,54 @@ class CayleyTrainer:
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
         self.t = 0
 
-    def step(self):
+    def step(self, events=None):
+        """One training step.  events (optional list) receives a CUDA event before each part
+        and one after the last, on the current stream (for a per-part time split)."""
         n3 = self.shape[2]
         dt = _DT[self.dtype]
+
+        def mark():
+            if events is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                events.append(e)
+
+        mark()
         N.tsvdm_cayley(n3, dt, self.A, self.M0, self.M, self.Z, self.Q, self.work)
+        mark()
         N.tsvdm_fixed_rank(self.plan.handle, self.X, self.M, self.k, self.U, self.S, self.V, 0,
                            want_rel_err=False)
+        mark()
         N.tsvdm_backward(self.plan.handle, self.X, self.M, self.k, self.U, self.S, self.V, 1.0,
                          self.dX, self.dM, self.loss)
+        mark()
         N.tsvdm_cayley_backward(n3, dt, self.M0, self.Z, self.Q, self.dM, self.dA, self.work)
         self.t += 1
+        mark()
         N.tsvdm_adam(n3 * n3, dt, self.A, self.dA, self.m1, self.m2, self.t, self.lr,
                      self.betas[0], self.betas[1], self.eps)
+        mark()
         return self.loss
+
+    PARTS = ("cayley", "forward_fixed_rank", "backward", "cayley_backward", "adam")
+
+    def part_split(self, steps=5):
+        """Mean milliseconds of each part of a step over `steps` further steps."""
+        acc = [0.0] * len(self.PARTS)
+        for _ in range(steps):
+            ev = []
+            self.step(ev)
+            torch.cuda.synchronize()
+            for i in range(len(self.PARTS)):
+                acc[i] += ev[i].elapsed_time(ev[i + 1]) / steps
+        return dict(zip(self.PARTS, acc))
+
+    def current_transform(self, out=None):
+        """M = Cayley(A) M0 for the current parameters."""
+        n3 = self.shape[2]
+        out = out if out is not None else torch.empty_like(self.A)
+        N.tsvdm_cayley(n3, _DT[self.dtype], self.A, self.M0, out, self.Z, self.Q, self.work)
+        return out
 
     def train(self, steps, record=True):
         """Runs `steps` steps; returns (losses, ms_per_step) timed with CUDA events."""

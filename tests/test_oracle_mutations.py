@@ -198,3 +198,20 @@ def test_data_driven_transform_transposed_is_caught(monkeypatch):
 
     monkeypatch.setattr(oracle, "data_transform", data_transform)
     assert _fails(pins.test_data_transform_diagonalises_the_mode3_gram)
+
+
+# ---------------------------------------------------------------- storage count (Sec. 3.4)
+def test_variable_ratio_without_slice_count_is_caught(monkeypatch):
+    def cr(m, p, ranks, with_sigma=True):           # the n of the input entries dropped
+        tot = float(np.sum(ranks)) * (m + p + (1 if with_sigma else 0))
+        return (m * p) / tot if tot > 0 else math.inf
+
+    monkeypatch.setattr(oracle, "compression_ratio_variable", cr)
+    assert _fails(pins.test_compression_ratio_variable_hand_worked)
+
+
+def test_variable_ratio_without_sigma_entries_is_caught(monkeypatch):
+    real = oracle.compression_ratio_variable
+    monkeypatch.setattr(oracle, "compression_ratio_variable",
+                        lambda m, p, ranks, with_sigma=True: real(m, p, ranks, False))
+    assert _fails(pins.test_compression_ratio_variable_hand_worked)

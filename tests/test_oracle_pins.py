@@ -260,6 +260,19 @@ def test_alg2_degenerate_cases():
 
 
 # ---------------------------------------------------------------- storage (Sec. 3.4, 4)
+def test_compression_ratio_variable_hand_worked():
+    """The variable-rank storage count of Sec. 3.4 by hand: three 3 x 2 slices (18 input
+    entries) with ranks 1, 0, 2 keep three triplets of 3 + 2 (+ 1 singular value)
+    entries; uniform ranks give the t-SVDM-I ratio; keeping nothing is unbounded."""
+    assert oracle.compression_ratio_variable(3, 2, [1, 0, 2]) == 18 / 18
+    assert oracle.compression_ratio_variable(3, 2, [1, 0, 2], with_sigma=False) == 18 / 15
+    assert oracle.compression_ratio_variable(4, 5, [2, 1]) == 40 / 30      # 3 x (4 + 5 + 1)
+    for m, p, n, k in [(73, 144, 5, 1), (253, 253, 3, 20), (300, 400, 2, 150)]:
+        v = oracle.compression_ratio_variable(m, p, [k] * n)
+        assert abs(v - oracle.compression_ratio_fixed(m, p, n, k)) <= 1e-12 * v
+    assert oracle.compression_ratio_variable(3, 2, [0, 0]) == float("inf")
+
+
 def test_compression_ratios_match_paper():
     with open(os.path.join(GOLDEN, "compression_ratios.txt")) as f:
         for line in f:
