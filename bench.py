@@ -508,10 +508,13 @@ def cfd_measure(args, stream):
     out = {"workload": "CFD-shaped 2048x256x512 FP32 (40 travelling waves, 1e-4 noise), "
                        "DCT-II, t-SVDM-I k=32", "oracle_sample_slices": len(which)}
     res = {}
-    for prec in ("bf16x3", "tf32", "fp64"):
+    for prec in ("bf16x3", "tf32", "dct2", "fp64"):
         dt = torch.float64 if prec == "fp64" else torch.float32
         Xp, Mp = (X.double(), M.double()) if prec == "fp64" else (X, M)
-        plan = Plan(n1, n2, n3, dtype=dt, prec=prec, orthogonal=True, stream=stream)
+        plan = Plan(n1, n2, n3, dtype=dt, prec="fp32" if prec == "dct2" else prec,
+                    orthogonal=True, stream=stream)
+        if prec == "dct2":
+            plan.set_transform("dct2")        # the fast DCT-II kernel instead of the TTM
         U = torch.empty(n3, k, n1, dtype=dt, device="cuda")
         S = torch.empty(n3, k, dtype=dt, device="cuda")
         V = torch.empty(n3, k, n2, dtype=dt, device="cuda")
@@ -538,7 +541,7 @@ def cfd_measure(args, stream):
         d["ttm_hbm"] = {"achieved": byts / (ttm_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                         "unit": "GB/s", "frac": byts / (ttm_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                         "peak_source": "of " + src}
-        if prec != "fp64":
+        if prec in ("bf16x3", "tf32"):
             terms = 3 if prec == "bf16x3" else 1
             flops = terms * 2.0 * P * n3 * n3
             peak = pr["bf16_mma"] if prec == "bf16x3" else pr["tf32_mma"]
@@ -567,7 +570,7 @@ def cfd_measure(args, stream):
         del U, S, V
         torch.cuda.empty_cache()
     S64 = res["fp64"][1]
-    for prec in ("bf16x3", "tf32", "fp64"):
+    for prec in ("bf16x3", "tf32", "dct2", "fp64"):
         d, Sg = res[prec]
         if prec != "fp64":
             d["vs_fp64_gpu"] = {"rel_err_diff": abs(d["rel_err"] - res["fp64"][0]["rel_err"]),

@@ -24,8 +24,9 @@
  *            staging buffers the plan allocates on the first such call and keeps.
  *            Calls that allocate device memory after plan creation (each once per
  *            plan, kept until tsvdm_plan_destroy): the first host-pointer call (staging),
- *            tsvdm_data_transform (its one-slice plan), tsvdm_plan_set_warm_start (enable)
- *            and tsvdm_plan_set_vectors (SECOND_PASS); tsvdm_probe_peak allocates and frees
+ *            tsvdm_data_transform (its one-slice plan), tsvdm_plan_set_warm_start (enable),
+ *            tsvdm_plan_set_vectors (SECOND_PASS) and tsvdm_plan_set_transform (DCT2
+ *            tables); tsvdm_probe_peak allocates and frees
  *            a status word.  Every other call allocates nothing.
  *   Streams  work is enqueued on the plan's stream.  Calls return once the work is
  *            enqueued, except where a host output (rel_err, total_rank, loss) is
@@ -217,6 +218,23 @@ tsvdm_status tsvdm_plan_set_angle_precision(tsvdm_plan plan, int angles);
  * themselves); ENOMEM if that fails.  EINVAL for other values. */
 typedef enum { TSVDM_VECTORS_ACCUMULATE = 0, TSVDM_VECTORS_SECOND_PASS = 1 } tsvdm_vectors;
 tsvdm_status tsvdm_plan_set_vectors(tsvdm_plan plan, int mode);
+
+/* Transform of the plan (Sec. 2.2; the paper's transform is the orthonormal DCT, which can
+ * be applied in O(n log n) instead of as a dense product):
+ *   TSVDM_TRANSFORM_DENSE  (default) the caller's M, as a dense mode-3 product (TTM);
+ *   TSVDM_TRANSFORM_DCT2   the orthonormal DCT-II, M(i, t) = s_i cos(pi i (2t + 1) / (2n))
+ *                          with s_0 = sqrt(1/n), s_i = sqrt(2/n), and its transpose for
+ *                          inverse transforms, by a fast kernel (an n-point FFT of each
+ *                          mode-3 fiber in shared memory; one read and one write of the
+ *                          tensor); on d-way plans one DCT-II per trailing mode.  The M
+ *                          arguments of the decompositions, transforms and reconstruction
+ *                          must still be non-NULL but are not read; tsvdm_backward, whose
+ *                          gradient is with respect to a dense M, reads and uses M.
+ * DCT2 needs an orthogonal plan (EINVAL otherwise) and every transformed mode length a
+ * power of two <= 4096 (ENOTSUP otherwise); it allocates the twiddle tables (about 3 n
+ * complex values per mode) once.  EINVAL for other values. */
+typedef enum { TSVDM_TRANSFORM_DENSE = 0, TSVDM_TRANSFORM_DCT2 = 1 } tsvdm_transform_kind;
+tsvdm_status tsvdm_plan_set_transform(tsvdm_plan plan, int kind);
 
 /* Bound of the waits of the tensor-core slice-SVD kernel's scheduler (a worker waiting for
  * the two column blocks of its block pair, or for work to appear): after `polls` polls

@@ -44,6 +44,11 @@ struct tsvdm_plan_s {
   int angle32 = 0;           // FP32 slices: rotation test and angle in FP32 (opt-in)
   long long wait_polls = 0;  // bound of the tensor-core Jacobi's scheduler waits (0: default)
   int vec_mode = 0;          // TSVDM_VECTORS_ACCUMULATE / TSVDM_VECTORS_SECOND_PASS
+  // TSVDM_TRANSFORM_DCT2: transforms by the orthonormal DCT-II through the fast kernels,
+  // with twiddle tables per transformed mode (element offsets dct_off[m] into dct_tab)
+  int xform = 0;
+  void *dct_tab = nullptr;
+  int64_t dct_off[TSVDM_MAX_ORDER] = {};
   int twopass = 0;           // the last decomposition ran without right vectors
   // second pass: one restricted-Jacobi entry per slice with kept columns (device arrays of
   // n3 entries, their host images, and the restricted Jacobi's sweep counts)
@@ -214,15 +219,21 @@ tsvdm_status transform_dway(tsvdm_plan_s *p, const T *X, int64_t P0, const T *M,
     const T *Mm = M + p->mo[m];
     const double *scale = nullptr;
     bool transB = false;
-    if (inverse && p->ortho) {
+    if (inverse && p->ortho && p->xform != TSVDM_TRANSFORM_DCT2) {
       CK(inv_scale<T>(Mm, nm, p->scal + SC_INVSCALE, p->st));
       scale = p->scal + SC_INVSCALE;
       transB = true;
       ++nl;
     }
-    for (int64_t q = 0; q < Qm; ++q) {
-      CK(ttm_n<T>(p, src + q * Pm * nm, Pm, nm, Mm, transB, dst + q * Pm * nm, scale));
-      nl += (p->prec == TSVDM_P_TF32 || p->prec == TSVDM_P_BF16X3) ? 2 : 1;
+    if (p->xform == TSVDM_TRANSFORM_DCT2) {                      // M is not read
+      CK(dct_mode3<T>(src, Pm, nm, Qm, inverse, (const char *)p->dct_tab + p->dct_off[m], dst,
+                      p->st));
+      ++nl;
+    } else {
+      for (int64_t q = 0; q < Qm; ++q) {
+        CK(ttm_n<T>(p, src + q * Pm * nm, Pm, nm, Mm, transB, dst + q * Pm * nm, scale));
+        nl += (p->prec == TSVDM_P_TF32 || p->prec == TSVDM_P_BF16X3) ? 2 : 1;
+      }
     }
     src = dst;
     Pm *= nm;
@@ -237,6 +248,11 @@ tsvdm_status run_ttm(tsvdm_plan_s *p, const T *X, int64_t P, const T *M, bool in
   if (p->dw) return transform_dway<T>(p, X, P, M, inverse, Y);
   const int64_t n = p->n3;
   stage_begin(p, TSVDM_STAGE_TTM);
+  if (p->xform == TSVDM_TRANSFORM_DCT2 && !sumsq) {
+    CK(dct_mode3<T>(X, P, n, 1, inverse, p->dct_tab, Y, p->st));
+    stage_end(p, TSVDM_STAGE_TTM, 1);
+    return TSVDM_OK;
+  }
   int nl = 1;
   const bool tc = (p->prec == TSVDM_P_TF32 || p->prec == TSVDM_P_BF16X3);
   if (!inverse) {
@@ -589,7 +605,7 @@ tsvdm_status backward_impl(tsvdm_plan_s *p, const void *X, const void *M, int64_
 bool valid_plan(tsvdm_plan p) { return p != nullptr && p->Ahat != nullptr; }
 
 void free_plan(tsvdm_plan_s *p) {
-  void *bufs[] = {p->tp_desc, p->tp_off, p->tp_sweeps, p->tp_sig, p->tp_perm, p->Ahat, p->Wt, p->Vw, p->sig, p->keys,
+  void *bufs[] = {p->dct_tab, p->tp_desc, p->tp_off, p->tp_sweeps, p->tp_sig, p->tp_perm, p->Ahat, p->Wt, p->Vw, p->sig, p->keys,
                   p->perm, p->sweeps, p->status,
                   p->queue, p->ranks_ws, p->off_ws, p->rots, p->scal, p->splitk, p->tc_ws,
                   p->norm2, p->sched, p->dtmp, p->warm_buf};
@@ -841,6 +857,70 @@ tsvdm_status tsvdm_plan_set_vectors(tsvdm_plan plan, int mode) {
     }
   }
   plan->vec_mode = mode;
+  plan->tol_valid = 0;
+  return TSVDM_OK;
+}
+
+tsvdm_status tsvdm_plan_set_transform(tsvdm_plan plan, int kind) {
+  if (!valid_plan(plan)) return TSVDM_EINVAL;
+  if (kind == TSVDM_TRANSFORM_DENSE) {
+    plan->xform = kind;
+    plan->tol_valid = 0;
+    return TSVDM_OK;
+  }
+  if (kind != TSVDM_TRANSFORM_DCT2 || !plan->ortho) return TSVDM_EINVAL;
+  const int modes = plan->dw ? plan->dw : 1;
+  int64_t len[TSVDM_MAX_ORDER];
+  int64_t pairs = 0;
+  for (int m = 0; m < modes; ++m) {
+    len[m] = plan->dw ? plan->td[m] : plan->n3;
+    if (len[m] < 1 || len[m] > 4096 || (len[m] & (len[m] - 1)) != 0) return TSVDM_ENOTSUP;
+    pairs += dct_table_pairs(len[m]);
+  }
+  // twiddle tables, computed in double precision and stored in the plan's precision
+  std::vector<double> h((size_t)pairs * 2);
+  int64_t off[TSVDM_MAX_ORDER];
+  int64_t at = 0;
+  const double pi = 3.14159265358979323846;
+  for (int m = 0; m < modes; ++m) {
+    off[m] = at;
+    const int64_t n = len[m], nh = n > 1 ? n / 2 : 1;
+    double *fw = h.data() + 2 * at, *iw = fw + 2 * nh, *post = iw + 2 * nh, *pre = post + 2 * n;
+    for (int64_t j = 0; j < nh; ++j) {
+      const double a = 2.0 * pi * (double)j / (double)n;
+      fw[2 * j] = cos(a);
+      fw[2 * j + 1] = -sin(a);
+      iw[2 * j] = cos(a);
+      iw[2 * j + 1] = sin(a);
+    }
+    for (int64_t k = 0; k < n; ++k) {
+      const double sk = sqrt((k == 0 ? 1.0 : 2.0) / (double)n);
+      const double a = pi * (double)k / (2.0 * (double)n);
+      post[2 * k] = sk * cos(a);
+      post[2 * k + 1] = -sk * sin(a);
+      pre[2 * k] = cos(a) / (sk * (double)n);
+      pre[2 * k + 1] = sin(a) / (sk * (double)n);
+    }
+    at += dct_table_pairs(n);
+  }
+  const size_t bytes = (size_t)pairs * 2 * plan->esz;
+  if (plan->dct_tab) cudaFree(plan->dct_tab);
+  plan->dct_tab = nullptr;
+  if (cudaMalloc(&plan->dct_tab, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return TSVDM_ENOMEM;
+  }
+  cudaError_t e;
+  if (plan->dtype == TSVDM_F64) {
+    e = cudaMemcpy(plan->dct_tab, h.data(), bytes, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> f(h.size());
+    for (size_t i = 0; i < h.size(); ++i) f[i] = (float)h[i];
+    e = cudaMemcpy(plan->dct_tab, f.data(), bytes, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  for (int m = 0; m < modes; ++m) plan->dct_off[m] = off[m] * 2 * (int64_t)plan->esz;
+  plan->xform = kind;
   plan->tol_valid = 0;
   return TSVDM_OK;
 }

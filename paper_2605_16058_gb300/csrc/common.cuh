@@ -49,6 +49,16 @@ cudaError_t ttm_tc(const float *X, int64_t P, int64_t n, const float *M, int64_t
                    const double *scale_ptr, const double *beta_ptr, const float *Z, int *status,
                    cudaStream_t st);
 
+// Orthonormal DCT-II (inverse: its transpose, DCT-III) along mode 3 of `batch` consecutive
+// P x n column-major views (view q at X + q P n), n a power of two <= 4096, from the
+// twiddle tables of dct_tables (device); Y must not overlap X.
+template <typename T>
+cudaError_t dct_mode3(const T *X, int64_t P, int64_t n, int64_t batch, bool inverse,
+                      const void *tables, T *Y, cudaStream_t st);
+// Elements (complex pairs) of the tables of one mode length n: n/2 forward and n/2 inverse
+// FFT twiddles, n post-twiddles (forward) and n pre-twiddles (inverse).
+inline int64_t dct_table_pairs(int64_t n) { return 2 * (n > 1 ? n / 2 : 1) + 2 * n; }
+
 // Transposed copy of each m x p slice (rows x cols) into p x m.
 template <typename T>
 cudaError_t transpose_slices(const T *A, int64_t m, int64_t p, int64_t nslices, T *B,

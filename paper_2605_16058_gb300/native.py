@@ -38,6 +38,7 @@ SIGNATURES = {
     "tsvdm_plan_set_angle_precision": (_i32, [_vp, _i32]),
     "tsvdm_plan_set_wait_limit": (_i32, [_vp, _i64]),
     "tsvdm_plan_set_vectors": (_i32, [_vp, _i32]),
+    "tsvdm_plan_set_transform": (_i32, [_vp, _i32]),
     "tsvdm_probe_peak": (_i32, [_i32, _i64, _vp, _pdbl]),
     "tsvdm_data_transform": (_i32, [_vp, _vp, _vp]),
     "tsvdm_transform": (_i32, [_vp, _vp, _vp, _i32, _vp]),
@@ -168,6 +169,15 @@ VECTORS = {"accumulate": VECTORS_ACCUMULATE, "second_pass": VECTORS_SECOND_PASS}
 def tsvdm_plan_set_vectors(plan, mode):
     m = VECTORS[mode] if isinstance(mode, str) else int(mode)
     return check(lib().tsvdm_plan_set_vectors(plan, m), "tsvdm_plan_set_vectors")
+
+
+TRANSFORM_DENSE, TRANSFORM_DCT2 = 0, 1
+TRANSFORMS = {"dense": TRANSFORM_DENSE, "dct2": TRANSFORM_DCT2}
+
+
+def tsvdm_plan_set_transform(plan, kind):
+    k = TRANSFORMS[kind] if isinstance(kind, str) else int(kind)
+    return check(lib().tsvdm_plan_set_transform(plan, k), "tsvdm_plan_set_transform")
 
 
 def tsvdm_plan_set_wait_limit(plan, polls):

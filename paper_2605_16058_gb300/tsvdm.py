@@ -112,6 +112,11 @@ class Plan:
         "second_pass" (singular values first, then the kept triplets' other side)."""
         N.tsvdm_plan_set_vectors(self.handle, mode)
 
+    def set_transform(self, kind):
+        """"dense" (the given M, default) or "dct2" (the orthonormal DCT-II by a fast kernel;
+        M arguments are then not read)."""
+        N.tsvdm_plan_set_transform(self.handle, kind)
+
     def set_wait_limit(self, polls):
         """Bound (polls) of the tensor-core slice-SVD kernel's scheduler waits; 0 = default."""
         N.tsvdm_plan_set_wait_limit(self.handle, polls)

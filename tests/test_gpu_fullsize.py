@@ -12,7 +12,8 @@
       against the threshold tau give the GPU's ranks (slices holding a sigma^2 within 1e-6
       relative of tau excepted); the error over those slices' energy, at those ranks,
       matches the oracle's within 1e-5.
-  cfd 2048x256x512 FP32, DCT-II, t-SVDM-I k = 32 with the BF16x3 and TF32 tensor-core TTMs:
+  cfd 2048x256x512 FP32, DCT-II, t-SVDM-I k = 32 with the BF16x3 and TF32 tensor-core TTMs
+  and the fast DCT-II transform:
     32 sampled slices against the oracle as above, and the BF16x3 relative error within
     1e-5 of the FP32 CUDA-core path's.
   crystal 512x256x128 FP32, DCT-II, k = 16 (learned-transform workload): loss (1e-4) and
@@ -135,14 +136,18 @@ def cfd_oracle():
     return dict(X=X, M=M, which=which, U=U_o, S=S_o)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "dct2"])
 def test_cfd_fixed_rank_full_size(cfd_oracle, prec):
+    """dct2: the fast DCT-II transform (FP32 FFT) in place of the dense TTM."""
     from paper_2605_16058_gb300.tsvdm import Plan
     n1, n2, n3 = CFD
     k = 32
     X, M, which = cfd_oracle["X"], cfd_oracle["M"], cfd_oracle["which"]
     Xd, Md = t_lib(X), t_lib(M)
-    plan = Plan(n1, n2, n3, dtype=torch.float32, prec=prec)
+    plan = Plan(n1, n2, n3, dtype=torch.float32, prec="fp32" if prec == "dct2" else prec)
+    if prec == "dct2":
+        plan.set_transform("dct2")
+        prec = "bf16x3"              # the same tolerances as the BF16x3 TTM
     out = plan.fixed_rank(Xd, Md, k)
     S_g, U_g = np_lib(out["S"]), np_lib(out["U"])
     U_o, S_o = cfd_oracle["U"], cfd_oracle["S"]
