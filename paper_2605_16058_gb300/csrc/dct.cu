@@ -25,6 +25,12 @@ template <typename T> struct Cx { T re, im; };
 
 constexpr int DT = 256;
 
+// Position of element i of a fiber in shared memory: one padding element after every 16
+// (a complex value spans two banks, so 16 of them fill the 32 banks): the FFT passes, whose
+// register groups gather elements 2^blo apart, then meet at most 2-way bank conflicts
+// instead of up to 32-way.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
 template <typename T>
 __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
@@ -46,7 +52,7 @@ __device__ __forceinline__ void dif_pass(Cx<T> *buf, int ld, int R, int n, int L
     Cx<T> *f = buf + (int64_t)r * ld;
     Cx<T> v[NM];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) v[m] = f[base + (m << blo)];
+    for (int m = 0; m < NM; ++m) v[m] = f[pad(base + (m << blo))];
 #pragma unroll
     for (int st = 0; st < A; ++st) {
       const int s = s0 + st;
@@ -62,7 +68,7 @@ __device__ __forceinline__ void dif_pass(Cx<T> *buf, int ld, int R, int n, int L
       }
     }
 #pragma unroll
-    for (int m = 0; m < NM; ++m) f[base + (m << blo)] = v[m];
+    for (int m = 0; m < NM; ++m) f[pad(base + (m << blo))] = v[m];
   }
 }
 
@@ -80,8 +86,8 @@ __global__ void __launch_bounds__(DT) dct_kernel(const T *__restrict__ X, int64_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);                 // n/2 (max 1)
   Cx<T> *pp = tw + (n > 1 ? n / 2 : 1);                             // n
-  Cx<T> *buf = pp + n;                                              // R x (n + 1)
-  const int ld = n + 1;
+  Cx<T> *buf = pp + n;                                              // R x ld
+  const int ld = pad(n) + 1;
   const int64_t r0 = (int64_t)blockIdx.x * R;
   const int64_t off = (int64_t)blockIdx.y * P * n;                  // batch of views
   const T *Xb = X + off;
@@ -98,9 +104,9 @@ __global__ void __launch_bounds__(DT) dct_kernel(const T *__restrict__ X, int64_
     const T x = row < P ? Xb[row + P * t] : T(0);
     if (!inverse) {
       const int j = (t & 1) ? n - 1 - (t >> 1) : (t >> 1);
-      buf[(int64_t)r * ld + j] = {x, T(0)};
+      buf[(int64_t)r * ld + pad(j)] = {x, T(0)};
     } else {
-      buf[(int64_t)r * ld + t] = {x, T(0)};
+      buf[(int64_t)r * ld + pad(t)] = {x, T(0)};
     }
   }
   __syncthreads();
@@ -110,15 +116,15 @@ __global__ void __launch_bounds__(DT) dct_kernel(const T *__restrict__ X, int64_
     for (int idx = threadIdx.x; idx < R * np; idx += DT) {
       const int r = idx / np, k = idx - r * np;
       Cx<T> *f = buf + (int64_t)r * ld;
-      const T yk = f[k < n ? k : 0].re;
+      const T yk = f[pad(k < n ? k : 0)].re;
       if (k == 0) {
         f[0] = {yk * pp[0].re, T(0)};
       } else if (2 * k == n) {
-        f[k] = cmul<T>(pp[k], {yk, -yk});
+        f[pad(k)] = cmul<T>(pp[k], {yk, -yk});
       } else if (k < n) {
-        const T ynk = f[n - k].re;
-        f[k] = cmul<T>(pp[k], {yk, -ynk});
-        f[n - k] = cmul<T>(pp[n - k], {ynk, -yk});
+        const T ynk = f[pad(n - k)].re;
+        f[pad(k)] = cmul<T>(pp[k], {yk, -ynk});
+        f[pad(n - k)] = cmul<T>(pp[n - k], {ynk, -yk});
       }
     }
     __syncthreads();
@@ -143,11 +149,11 @@ __global__ void __launch_bounds__(DT) dct_kernel(const T *__restrict__ X, int64_
     const Cx<T> *f = buf + (int64_t)r * ld;
     T y;
     if (!inverse) {
-      const Cx<T> v = f[brev(k, L)];
+      const Cx<T> v = f[pad(brev(k, L))];
       y = pp[k].re * v.re - pp[k].im * v.im;
     } else {
       const int j = (k & 1) ? n - 1 - (k >> 1) : (k >> 1);
-      y = f[brev(j, L)].re;
+      y = f[pad(brev(j, L))].re;
     }
     Yb[row + P * k] = y;
   }
@@ -162,7 +168,7 @@ int dct_rows_per_cta(int n) {
 
 size_t dct_smem_bytes(int n, size_t cx_bytes) {
   const int R = dct_rows_per_cta(n);
-  return cx_bytes * ((size_t)(n > 1 ? n / 2 : 1) + n + (size_t)R * (n + 1));
+  return cx_bytes * ((size_t)(n > 1 ? n / 2 : 1) + n + (size_t)R * (n + (n >> 4) + 1));
 }
 
 template <typename T>
