@@ -1378,13 +1378,14 @@ __global__ void __launch_bounds__(NT, NS == 2 ? 3 : 2) jacobi_kernel(JacobiParam
 // tickets are handed out in increasing order and a pair only waits for pairs with smaller
 // tickets, so the earliest unfinished ticket can always run (no deadlock).  The worker that
 // completes the last pair of a sweep closes it: the slice has converged if no pair rotated
-// (the stopping rule of the scalar method), else it copies the squared column norms the
-// sweep left into a per-slice snapshot and opens the next sweep's tickets (every worker
-// sorts the sweep's column order from the snapshot, so all agree on the blocks while the
-// sweep's own pairs keep updating the norms).  A worker takes the next ticket of its
-// current slice, else starts a new slice, else helps any open slice, and only takes a
-// ticket whose two blocks are already free (the pair then runs without waiting; the
-// earliest unfinished ticket always becomes free).  Every wait is bounded; on expiry the
+// (the stopping rule of the scalar method), else it sorts the columns by the squared norms
+// the sweep left (all of its pairs are done, so they are final), stores that order for the
+// slice in global memory and opens the next sweep's tickets; every worker takes its block
+// pair's columns from the stored order (the first sweep uses the natural order).  A worker
+// takes the next ticket of its current slice, else starts a new slice, else helps any open
+// slice (warp 0 of the worker examines 32 slices at a time), and only takes a ticket whose
+// two blocks are already free, so the pair runs without waiting (the earliest unfinished
+// ticket always becomes free; versions only grow).  Every wait is bounded; on expiry the
 // kernel raises a global abort flag and ST_TIMEOUT.
 constexpr int TC_GROUPS = 3;
 constexpr uint32_t TC_COLS = 256;     // TMEM columns of the CTA (64 per group, power of two)
@@ -1421,7 +1422,7 @@ __device__ __forceinline__ unsigned long long vload64(const unsigned long long *
 __device__ bool take_ticket(SliceCtx *ctx, const int *ver, int nbmax, const JacobiParams &p,
                             int sl, int &sweep, int &t) {
   SliceCtx &c = ctx[sl];
-  if (vload(&c.finished)) return false;
+  // (a finished slice has handed out all tickets of its last sweep: tk >= total below)
   const int cols = p.desc ? p.desc[sl].cols : p.cols;
   const int nb = tc_blocks(cols), np = nb / 2;
   const unsigned total = (unsigned)(np * (nb - 1));
@@ -1447,6 +1448,49 @@ __device__ bool take_ticket(SliceCtx *ctx, const int *ver, int nbmax, const Jaco
   return false;
 }
 
+// Warp-wide search over the started slices (every lane of the calling warp): lane l looks
+// at slice (first + base + l) mod started for base = 0, 32, ..; the lowest lane that sees a
+// free ticket tries to take it.  Returns the slice (ticket in sweep, t; same in all lanes),
+// or -1.
+__device__ int scan_tickets(SliceCtx *ctx, const int *ver, int nbmax, const JacobiParams &p,
+                            int first, int started, int &sweep, int &t) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < started; base += 32) {
+    const int k = base + lane;
+    const int cand = k < started ? (first + k) % started : -1;
+    bool free = false;
+    if (cand >= 0) {
+      const unsigned long long sn = vload64(&ctx[cand].sn);
+      const int w = (int)(sn >> 32);
+      const unsigned tk = (unsigned)sn;
+      const int cols = p.desc ? p.desc[cand].cols : p.cols;
+      const int nb = tc_blocks(cols), np = nb / 2;
+      if (w != 0 && tk < (unsigned)(np * (nb - 1))) {
+        const int round = (int)(tk / np), q = (int)(tk % np);
+        int bi, bj;
+        rr_pair(nb, round, q, bi, bj);
+        const int need = (w - 1) * (nb - 1) + round;
+        const int *v = ver + (int64_t)cand * nbmax;
+        free = vload(v + bi) >= need && vload(v + bj) >= need;
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, free);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      int got = 0, w = 0, tt = 0;
+      if (lane == src) got = take_ticket(ctx, ver, nbmax, p, cand, w, tt) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, src);
+      if (got) {
+        sweep = __shfl_sync(0xffffffffu, w, src);
+        t = __shfl_sync(0xffffffffu, tt, src);
+        return __shfl_sync(0xffffffffu, cand, src);
+      }
+      m &= m - 1;
+    }
+  }
+  return -1;
+}
+
 __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiParams p) {
   constexpr int W2 = SmemTc::W2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1467,7 +1511,7 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
   SliceCtx *ctx = reinterpret_cast<SliceCtx *>(hdr + 1);
   const int nbmax = tc_blocks(p.max_cols);
   int *ver = reinterpret_cast<int *>(ctx + p.nslices);
-  float *snap = reinterpret_cast<float *>(ver + (int64_t)p.nslices * nbmax);
+  int *ordg = reinterpret_cast<int *>(ver + (int64_t)p.nslices * nbmax);   // column orders
   if (tid == 0) {
     for (int b = 0; b < 3; ++b) tc::mbar_init(&s.bar[b], 1);
     tc::mbar_init_fence();
@@ -1481,57 +1525,61 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
   gbar.sync();
 
   uint32_t phase = 0;
-  int cur = -1;                        // slice this worker prefers (tid 0's view)
+  int cur = -1;                        // slice this worker prefers (warp 0's view)
   bool queue_open = true;
-  int cache_slice = -1, cache_sweep = 0;   // column order held in s.ord
   const int worker = blockIdx.x * TC_GROUPS + g;
   for (;;) {
-    // ---- tid 0 finds the next work item and broadcasts it
-    if (tid == 0) {
+    // ---- warp 0 finds the next work item (lane 0 decides) and broadcasts it
+    if (tid < 32) {
       int kind = WK_EXIT, sl = -1, w = 0, t = 0;
       for (unsigned idle = 0;; ++idle) {
-        if (vload(&hdr->abort)) break;
-        if (cur >= 0 && take_ticket(ctx, ver, nbmax, p, cur, w, t)) {
-          kind = WK_PAIR;
-          sl = cur;
-          break;
-        }
-        if (queue_open) {
-          const int n = atomicAdd(p.queue, 1);
-          if (n < p.nslices) {
-            kind = WK_START;
-            sl = n;
-            break;
+        int stop = 0;
+        if (tid == 0) {
+          stop = vload(&hdr->abort);
+          if (!stop && cur >= 0 && take_ticket(ctx, ver, nbmax, p, cur, w, t)) {
+            kind = WK_PAIR;
+            sl = cur;
+          } else if (!stop && queue_open) {
+            const int n = atomicAdd(p.queue, 1);
+            if (n < p.nslices) {
+              kind = WK_START;
+              sl = n;
+            } else {
+              queue_open = false;
+            }
           }
-          queue_open = false;
         }
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        kind = __shfl_sync(0xffffffffu, kind, 0);
+        if (stop || kind != WK_EXIT) break;
         const int started = min(vload(p.queue), p.nslices);
-        bool got = false;
-        for (int k = 0; k < started && !got; ++k) {
-          const int cand = (worker + k) % started;
-          if (take_ticket(ctx, ver, nbmax, p, cand, w, t)) {
-            got = true;
-            sl = cand;
-          }
-        }
-        if (got) {
+        const int got = scan_tickets(ctx, ver, nbmax, p, worker % (started > 0 ? started : 1),
+                                     started, w, t);
+        if (got >= 0) {
           kind = WK_PAIR;
-          cur = sl;
+          sl = got;
+          cur = got;
           break;
         }
-        if (vload(&hdr->fin) >= p.nslices) break;
+        int fin = 0;
+        if (tid == 0) fin = vload(&hdr->fin) >= p.nslices;
+        if (__shfl_sync(0xffffffffu, fin, 0)) break;
         if (idle >= spin) {
-          atomicExch(&hdr->abort, 1);
-          s.fail = 1;
+          if (tid == 0) {
+            atomicExch(&hdr->abort, 1);
+            s.fail = 1;
+          }
           break;
         }
         __nanosleep(1000);
       }
-      __threadfence();                 // what the ticket's publisher wrote is visible
-      s.wk[0] = kind;
-      s.wk[1] = sl;
-      s.wk[2] = w;
-      s.wk[3] = t;
+      if (tid == 0) {
+        __threadfence();               // what the ticket's publisher wrote is visible
+        s.wk[0] = kind;
+        s.wk[1] = sl;
+        s.wk[2] = w;
+        s.wk[3] = t;
+      }
     }
     gbar.sync();
     const int kind = s.wk[0], slice = s.wk[1], sweep = s.wk[2], ticket = s.wk[3];
@@ -1558,29 +1606,19 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
     int bi, bj;
     rr_pair(nb, round, q, bi, bj);
     const bool sorted = v.nrm2 != nullptr && v.cols <= MAXSORT;
-    if (sorted && (cache_slice != slice || cache_sweep != sweep)) {
-      sort_columns(s, snap + (int64_t)slice * p.max_cols, v.cols, sweep == 1, tid, gbar);
-      cache_slice = slice;
-      cache_sweep = sweep;
-    }
+    // both blocks have finished the previous round (checked when the ticket was taken)
     if (tid == 0) {
-      // both blocks must have finished the previous round
-      const int need = (sweep - 1) * (nb - 1) + round;
-      const int *vi = ver + (int64_t)slice * nbmax + bi, *vj = ver + (int64_t)slice * nbmax + bj;
-      for (unsigned it = 0; vload(vi) < need || vload(vj) < need; ++it) {
-        if (vload(&hdr->abort)) break;
-        if (it >= spin) {
-          atomicExch(&hdr->abort, 1);
-          s.fail = 1;
-          break;
-        }
-        __nanosleep(256);
-      }
-      __threadfence();
       s.nrot = 0;
       s.nonfinite = 0;
     }
-    pair_columns<W2>(s, bi, bj, v.cols, sorted, tid);
+    if (tid < W2) {
+      // this pair's columns in the sweep's order (natural in the first sweep)
+      constexpr int B = W2 / 2;
+      const int lc = (tid < B) ? bi * B + tid : bj * B + (tid - B);
+      s.col[tid] = lc < v.cols ? (sorted && sweep > 1 ? __ldcg(ordg + (int64_t)slice * p.max_cols + lc)
+                                                      : lc)
+                               : -1;
+    }
     gbar.sync();
     // the first round of a sweep also rotates within each block (full inner sweeps), the
     // others only across the two blocks
@@ -1634,10 +1672,11 @@ __global__ void __launch_bounds__(NT * TC_GROUPS, 1) jacobi_tc_kernel(JacobiPara
     }
     gbar.sync();
     if (s.reopen) {
-      // the next sweep: snapshot of the norms this sweep left, then its tickets
+      // the next sweep: the column order by the norms this sweep left, then its tickets
       if (sorted) {
-        float *sn = snap + (int64_t)slice * p.max_cols;
-        for (int k = tid; k < v.cols; k += NT) __stcg(sn + k, __ldcg(v.nrm2 + k));
+        sort_columns(s, v.nrm2, v.cols, false, tid, gbar);
+        int *og = ordg + (int64_t)slice * p.max_cols;
+        for (int k = tid; k < v.cols; k += NT) __stcg(og + k, s.ord[k]);
       }
       __threadfence();
       gbar.sync();
@@ -1702,7 +1741,7 @@ cudaError_t launch_jacobi(const JacobiParams &p, cudaStream_t st, int cluster_hi
 size_t sched_bytes_for(int64_t nslices, int64_t max_cols) {
   return sizeof(SchedHdr) + (size_t)nslices * sizeof(SliceCtx) +
          (size_t)nslices * (size_t)tc_blocks((int)max_cols) * sizeof(int) +
-         (size_t)nslices * (size_t)max_cols * sizeof(float);
+         (size_t)nslices * (size_t)max_cols * sizeof(int);     // column orders
 }
 
 // grid_hint: CTAs (0 = one per SM).  The scheduler state is zeroed here, in stream order.
