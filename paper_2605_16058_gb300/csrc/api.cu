@@ -539,6 +539,19 @@ tsvdm_status pack_impl(tsvdm_plan_s *p, void *U, void *S, void *V) {
   return TSVDM_OK;
 }
 
+// C = alpha A^T B over the long mode: tensor cores for FP32 plans unless the FMA engine was
+// chosen (tsvdm_plan_set_engine) or the shape does not fit, CUDA cores otherwise.
+template <typename T>
+cudaError_t atb_any(tsvdm_plan_s *p, const T *A, const T *B, int64_t P, int64_t n, T *C,
+                    const double *alpha) {
+  if constexpr (sizeof(T) == 4) {
+    if (p->engine != JACOBI_FMA && atb_tc_supported((const float *)A, (const float *)B, P, n))
+      return atb_tc((const float *)A, (const float *)B, P, n, (float *)C, alpha, p->splitk,
+                    p->splitk_elems, p->status, p->st);
+  }
+  return gemm_atb<T>(A, B, P, n, C, alpha, p->splitk, p->splitk_elems, p->st);
+}
+
 // Out_i (+)= U_i diag(S_i) V_i^T: tensor cores for FP32 plans unless the FMA engine was
 // chosen (tsvdm_plan_set_engine), CUDA cores otherwise.
 template <typename T>
@@ -587,8 +600,7 @@ tsvdm_status backward_impl(tsvdm_plan_s *p, const void *X, const void *M, int64_
   }
   if (dM) {
     stage_begin(p, TSVDM_STAGE_OTHER);
-    CK(gemm_atb<T>((const T *)p->Ahat, (const T *)X, P, n, (T *)dM, p->scal + SC_ALPHA,
-                   p->splitk, p->splitk_elems, p->st));
+    CK(atb_any<T>(p, (const T *)p->Ahat, (const T *)X, P, n, (T *)dM, p->scal + SC_ALPHA));
     stage_end(p, TSVDM_STAGE_OTHER, 2);
   }
   if (loss && is_device_ptr(loss)) {
@@ -651,8 +663,7 @@ tsvdm_status data_transform_impl(tsvdm_plan_s *p, const void *X, void *M) {
   const T unit = T(1);
   CK(cudaMemcpyAsync(one, &unit, sizeof(T), cudaMemcpyHostToDevice, p->st));
   stage_begin(p, TSVDM_STAGE_OTHER);
-  CK(gemm_atb<T>((const T *)dX, (const T *)dX, P, n, G, nullptr, p->splitk, p->splitk_elems,
-                 p->st));
+  CK(atb_any<T>(p, (const T *)dX, (const T *)dX, P, n, G, nullptr));
   stage_end(p, TSVDM_STAGE_OTHER, 2);
   // G = W diag(sigma) W^T (symmetric PSD): the one-slice t-SVD with M = [1] gives W in U
   if ((s = fixed_rank_impl<T>(p->dsub, G, one, n, U, S, V, 0, nullptr)) != TSVDM_OK) return s;

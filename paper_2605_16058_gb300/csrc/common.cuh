@@ -200,6 +200,13 @@ template <typename T>
 cudaError_t gemm_atb(const T *A, const T *B, int64_t P, int64_t n, T *C, const double *alpha,
                      double *ws, size_t ws_elems, cudaStream_t st);
 
+// The same product for FP32 operands on the tensor cores (BF16x3, FP32 accumulation, FP64
+// split sums); n <= 512, P a multiple of 4, 16-byte aligned operands (atb_tc_supported).
+bool atb_tc_supported(const float *A, const float *B, int64_t P, int64_t n);
+cudaError_t atb_tc(const float *A, const float *B, int64_t P, int64_t n, float *C,
+                   const double *alpha, double *ws, size_t ws_elems, int *status,
+                   cudaStream_t st);
+
 template <typename T>
 cudaError_t sumsq(const T *X, int64_t count, double *out, cudaStream_t st);
 
