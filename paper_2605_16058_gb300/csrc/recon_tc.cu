@@ -33,6 +33,10 @@ struct ReconSmem {
   int fail;
 };
 
+// SS: ||Out||^2 is accumulated (FP64); a separate instantiation, so that the product
+// alone issues no FP64 instruction (predicated-off FP64 operations still occupy the FP64
+// pipe, which runs at a small fraction of the FP32 rate on this GPU).
+template <bool SS>
 __global__ void __launch_bounds__(RT, 1)
     slice_products_tc_kernel(const float *__restrict__ U, const float *__restrict__ S,
                              const float *__restrict__ V, const int64_t *__restrict__ offsets,
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(RT, 1)
             if (bcol < n2) {
               const float v = subtract ? O[a + n1 * bcol] - d[e] : d[e];
               O[a + n1 * bcol] = v;
-              if (sumsq) ss += (double)v * (double)v;   // FP64 only when it is asked for
+              if constexpr (SS) ss += (double)v * (double)v;
             }
           }
         }
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(RT, 1)
     tc::fence_before_sync();
     __syncthreads();                               // TMEM read before the next tile's MMAs
   }
-  if (sumsq) {
+  if constexpr (SS) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) atomicAdd(sumsq, ss);
@@ -212,8 +216,8 @@ cudaError_t slice_products_tc(const float *U, const float *S, const float *V,
                               int64_t n3, float *Out, bool subtract_from_out, double *sumsq,
                               int *status, cudaStream_t st, bool vtrans) {
   const size_t smem = sizeof(ReconSmem) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(slice_products_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = sumsq ? slice_products_tc_kernel<true> : slice_products_tc_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -222,8 +226,8 @@ cudaError_t slice_products_tc(const float *U, const float *S, const float *V,
   const int64_t ntiles = n3 * ((n1 + RM - 1) / RM) * ((n2 + RN - 1) / RN);
   if (ntiles == 0) return cudaSuccess;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  slice_products_tc_kernel<<<grid, RT, smem, st>>>(U, S, V, offsets, k, n1, n2, n3, Out,
-                                                  subtract_from_out, sumsq, status, vtrans);
+  kern<<<grid, RT, smem, st>>>(U, S, V, offsets, k, n1, n2, n3, Out, subtract_from_out, sumsq,
+                               status, vtrans);
   return cudaGetLastError();
 }
 
