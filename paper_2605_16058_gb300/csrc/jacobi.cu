@@ -331,8 +331,11 @@ __device__ __forceinline__ void inner_pair(bool full, int step, int k, int &i, i
 // decide64 puts single-precision products in front of the FP64 comparison: they carry
 // relative errors below 1e-6, so outside a 2% band around the threshold they give the FP64
 // answer, and the FP64 products run only inside the band (or when a single-precision
-// product over- or underflows).  The decision is always the FP64 one.
-__device__ __forceinline__ bool exceeds(double a, double b, double g, double tol2) {
+// product over- or underflows).  The decision is always the FP64 one.  The FP64 test is a
+// call, so that it stays a branch taken by the few lanes in the band: predicated FP64
+// instructions still occupy the FP64 pipe, whose rate is a small fraction of the FP32 rate
+// on this GPU.
+__device__ __noinline__ bool exceeds(double a, double b, double g, double tol2) {
   return isfinite(a) && isfinite(b) && g * g > tol2 * (a * b);
 }
 template <typename T>
@@ -382,22 +385,25 @@ __device__ __forceinline__ void angle64(double a, double b, double g, double &c,
 
 // The FP64 rotation angle of an FP32 slice's pair, with few FP64 operations (the FP64 rate
 // of the GPU is a small fraction of its FP32 rate).  The angle t = tan(theta) solves
-// g2 t^2 + 2 h t - g2 = 0 (t^2 + 2 zeta t - 1 = 0 times g2; h = b - a, g2 = 2 g), whose
-// derivative 2 (g2 t + h) has magnitude 2 sqrt(h^2 + g2^2) at the root: from the FP32
-// estimate t0 (absolute error d, |t| <= 1) one Newton step in FP64 arithmetic leaves about
-// d^2 / 2 plus the FP64 rounding of f(t0), ~1e-13.  The rotation then takes that angle in
-// the slice's precision: c = 1 / sqrt(1 + t^2), s = c t and the rotated diagonal a - t g,
-// b + t g from t rounded to FP32 (the values the FP32 rotation is applied with).
+// f(t) = g (t^2 - 1) + h t = 0 (t^2 + 2 zeta t - 1 = 0 times g; h = b - a), whose derivative
+// f'(t) = 2 g t + h has magnitude sqrt(h^2 + 4 g^2) at the root: from the FP32 estimate t0
+// (absolute error d, |t| <= 1) one Newton step leaves about d^2 / 2 plus the rounding of
+// f(t0).  f(t0) is the cancelling part and is evaluated in FP64 from the FP32 inputs (nine
+// FP64-pipe instructions, conversions included); the step f(t0) / f'(t0) is small against
+// t0 (|d| ~ 1e-7 |t|), so it is formed in FP32 from f(t0) rounded to FP32 and t = t0 - step
+// is the one FP32 rounding of the refined angle.  The rotation then takes that angle in the
+// slice's precision: c = 1 / sqrt(1 + t^2), s = c t and the rotated diagonal a - t g, b + t g
+// (the values the FP32 rotation is applied with).
 __device__ __forceinline__ void angle64_f32(float a, float b, float g, float &c, float &sn,
                                             float &da, float &db) {
   const float hf = b - a, g2f = 2.f * g;
   float t0 = fabsf(g2f) / (fabsf(hf) + hypotf(hf, g2f));
   if ((hf >= 0.f) != (g2f >= 0.f)) t0 = -t0;
-  const double gd = g, g2 = gd + gd, h = (double)b - (double)a, td = t0;
-  const double f = fma(g2, td * td, fma(h, (double)(2.f * t0), -g2));   // g2 t^2 + 2 h t - g2
-  const float fp = 2.f * fmaf(g2f, t0, hf);                      // f'(t0), FP32 suffices
-  const float rf = __frcp_rn(fp);     // |f'| >= 2 |g2| > 0; infinite only for denormal pairs
-  const float t = isfinite(rf) ? (float)fma(-f, (double)rf, td) : t0;
+  const double G = g, T = t0, H = (double)b - (double)a;
+  const float f = (float)fma(G, fma(T, T, -1.0), H * T);       // f(t0) in FP64, then rounded
+  const float rf = __frcp_rn(fmaf(g2f, t0, hf));   // 1 / f'(t0); |f'| >= 2 |g| > 0 (infinite
+                                                    // only for denormal pairs)
+  const float t = isfinite(rf) ? t0 - f * rf : t0;
   // correctly rounded 1/sqrt: an approximate reciprocal square root biased c (and the
   // column norms, over thousands of rotations) by ~1e-5
   c = __frsqrt_rn(fmaf(t, t, 1.f));
