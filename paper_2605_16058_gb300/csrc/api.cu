@@ -350,8 +350,19 @@ tsvdm_status second_pass(tsvdm_plan_s *p, int64_t k, const int *ranks, const int
   const int64_t kd = p->rows, od = p->cols, n3 = p->n3;
   T *Kout = tr ? V : U, *Oout = tr ? U : V;
   const int64_t maxr = ranks ? p->cols : k;
-  CK(complete_vectors<T>((const T *)p->Ahat, p->n1, p->n2, n3, tr, k, ranks, offsets, maxr, U,
-                         nullptr, V, p->st));
+  bool done_tc = false;
+  if constexpr (sizeof(T) == 4) {
+    // tensor cores (three-term BF16 split) unless the FMA engine was chosen
+    if (p->engine != JACOBI_FMA &&
+        complete_tc_supported((const float *)p->Ahat, (const float *)Kout, p->n1, p->n2, tr)) {
+      CK(complete_tc((const float *)p->Ahat, p->n1, p->n2, n3, k, ranks, offsets,
+                     (const float *)Kout, nullptr, (float *)Oout, p->status, p->st));
+      done_tc = true;
+    }
+  }
+  if (!done_tc)
+    CK(complete_vectors<T>((const T *)p->Ahat, p->n1, p->n2, n3, tr, k, ranks, offsets, maxr, U,
+                           nullptr, V, p->st));
   // the kept columns of every slice (ranks are read back: the descriptors are built here)
   p->tp_hranks.assign(n3, (int)k);
   if (ranks) {

@@ -200,6 +200,15 @@ template <typename T>
 cudaError_t gemm_atb(const T *A, const T *B, int64_t P, int64_t n, T *C, const double *alpha,
                      double *ws, size_t ws_elems, cudaStream_t st);
 
+// Z_i = A_i^T K_i diag(1 / S_i) of complete_vectors for FP32 slices in the column layout on
+// the tensor cores (three-term BF16 split, FP32-level accuracy); complete_tc_supported says
+// whether the layout and alignment allow it.
+bool complete_tc_supported(const float *Ahat, const float *K, int64_t n1, int64_t n2,
+                           bool transposed);
+cudaError_t complete_tc(const float *Ahat, int64_t n1, int64_t n2, int64_t nslices,
+                        int64_t k_uniform, const int *ranks, const int64_t *offsets,
+                        const float *K, const float *S, float *O, int *status, cudaStream_t st);
+
 // The same product for FP32 operands on the tensor cores (BF16x3, FP32 accumulation, FP64
 // split sums); n <= 512, P a multiple of 4, 16-byte aligned operands (atb_tc_supported).
 bool atb_tc_supported(const float *A, const float *B, int64_t P, int64_t n);
