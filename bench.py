@@ -185,7 +185,7 @@ def jacobi_traffic_per_slice():
     """DRAM bytes per slice of the Jacobi kernel from the committed ncu summary, or None
     when the kernel source changed since those counters were taken."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "jacobi_tc_kernel_climate_1024x512x304.md")
+    prof = os.path.join(ROOT, "profiles", "jacobi_tc_kernel_climate_1024x512x128.md")
     src = os.path.join(ROOT, "paper_2605_16058_gb300", "csrc", "jacobi.cu")
     try:
         txt = open(prof).read()
@@ -827,7 +827,7 @@ def main():
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": (None if jacobi_traffic_per_slice() is None
                                  else jacobi_traffic_per_slice() * n3),
-                     "traffic_note": "ncu dram bytes per slice (1024x512x304 capture) x slices",
+                     "traffic_note": "ncu dram bytes per slice (1024x512x128 capture) x slices",
                      "peak_source": fp32_src,
                      "note": "classical one-sided Jacobi flop count (3 m p (p-1) per sweep + "
                              "6 (m + p) per rotation) against the FP32 CUDA-core peak; the "
