@@ -29,10 +29,13 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("dt,case,tol", [(torch.float64, "smoke", 1e-9),
-                                         (torch.float32, "crystal", 1e-4),
-                                         (torch.float64, "crystal", 1e-9)])
-def test_backward_matches_oracle(dt, case, tol):
+@pytest.mark.parametrize("dt,case,tol,engine", [(torch.float64, "smoke", 1e-9, None),
+                                                (torch.float32, "crystal", 1e-4, None),
+                                                (torch.float32, "crystal", 1e-4, "fma"),
+                                                (torch.float64, "crystal", 1e-9, None)])
+def test_backward_matches_oracle(dt, case, tol, engine):
+    """FP32 dL/dM: tensor-core A^T B (default engine) and the CUDA-core split-K product
+    (FMA engine)."""
     from paper_2605_16058_gb300.tsvdm import Plan
     if case == "smoke":
         c = synth.smoke_case()
@@ -45,6 +48,8 @@ def test_backward_matches_oracle(dt, case, tol):
         M = M.astype(np.float32).astype(np.float64)
     n1, n2, n3 = X.shape
     plan = Plan(n1, n2, n3, dtype=dt)
+    if engine is not None:
+        plan.set_engine(engine)
     Xd, Md = t_lib(X, dtype=dt), t_lib(M, dtype=dt)
     f = plan.fixed_rank(Xd, Md, k)
     dX, dM = torch.empty_like(Xd), torch.empty_like(Md)

@@ -174,6 +174,15 @@ def test_fixed_rank_second_pass(name, shape, dt, k):
     _fixed_rank_case(name, shape, dt, k, vectors="second_pass")
 
 
+# The second pass's product Z = A^T U_k on both engines for FP32 slices: the tensor cores
+# (tall slices, K-major 16-byte loads, N = the kept count in multiples of 16) and the
+# CUDA-core tiled product (the FMA engine, and every wide slice).
+@pytest.mark.parametrize("engine", ["tc", "fma"])
+@pytest.mark.parametrize("name,shape,dt,k", CASES_ENGINE, ids=[c[0] for c in CASES_ENGINE])
+def test_fixed_rank_second_pass_each_engine(name, shape, dt, k, engine):
+    _fixed_rank_case(name, shape, dt, k, engine, vectors="second_pass")
+
+
 def test_engine_argument_errors():
     from paper_2605_16058_gb300 import native as N
     p64 = _plan(8, 8, 2, torch.float64)
@@ -422,12 +431,16 @@ def test_argument_errors():
 
 
 # ---------------------------------------------------------------- data-driven M
-@pytest.mark.parametrize("dt,shape", [(torch.float64, (60, 40, 12)),
-                                      (torch.float32, (200, 130, 24))])
-def test_data_transform_matches_oracle(dt, shape):
+@pytest.mark.parametrize("dt,shape,engine", [(torch.float64, (60, 40, 12), None),
+                                             (torch.float32, (200, 130, 24), None),
+                                             (torch.float32, (200, 130, 24), "fma"),
+                                             (torch.float32, (36, 20, 200), None)])
+def test_data_transform_matches_oracle(dt, shape, engine):
     """M from the library's Jacobi SVD of the mode-3 Gram against LAPACK's SVD of the
     unfolding: orthogonal, diagonalising the mode-3 Gram, the same rows (sign rule) where
-    the singular values are well separated, and the same t-SVDM-I error."""
+    the singular values are well separated, and the same t-SVDM-I error.  FP32 Grams run on
+    the tensor cores (n3 = 200: two bands of 128 rows, 256 padded columns) or, with the FMA
+    engine, on the CUDA cores."""
     rng = np.random.default_rng(43)
     n1, n2, n3 = shape
     X = synth.cp_tensor(n1, n2, n3, 8, rng, noise_rel=0.2)
@@ -435,6 +448,8 @@ def test_data_transform_matches_oracle(dt, shape):
         X = X.astype(np.float32).astype(np.float64)
     Mo, sig = oracle.data_transform(X)
     plan = _plan(n1, n2, n3, dt)
+    if engine is not None:
+        plan.set_engine(engine)     # the mode-3 Gram on the CUDA cores
     Xd = t_lib(X, dtype=dt)
     Mg = np_lib(plan.data_transform(Xd))
     tol = 1e-10 if dt == torch.float64 else 2e-5
