@@ -169,22 +169,28 @@ class Plan:
 class TruncationLoss(torch.autograd.Function):
     """L(X, M) = sqrt(sum of discarded sigma^2 of X x_3 M at rank k) / ||X||_F with the
     library's hand-written adjoint.  The forward pass runs t-SVDM-I and the residual
-    adjoint once (dL = 1) and keeps dX, dM; backward scales them by the upstream grad."""
+    adjoint once (dL = 1), forming only the gradients that are needed (none when neither X
+    nor M requires one: the loss alone); backward scales them by the upstream grad."""
 
     @staticmethod
     def forward(ctx, X, M, plan, k):
         f = plan.fixed_rank(X, M, k, rel_err=False)
-        dX = torch.empty_like(X)
-        dM = torch.empty_like(M)
+        need_x, need_m = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        dX = torch.empty_like(X) if need_x else None
+        dM = torch.empty_like(M) if need_m else None
         loss = torch.zeros(1, dtype=torch.float64, device=X.device)
         plan.backward(X, M, k, f["U"], f["S"], f["V"], 1.0, dX, dM, loss)
-        ctx.save_for_backward(dX, dM)
+        ctx.need = (need_x, need_m)
+        ctx.save_for_backward(*[t for t in (dX, dM) if t is not None])
         return loss[0]
 
     @staticmethod
     def backward(ctx, g):
-        dX, dM = ctx.saved_tensors
-        return dX * g.to(dX.dtype), dM * g.to(dM.dtype), None, None
+        saved = list(ctx.saved_tensors)
+        dX = saved.pop(0) if ctx.need[0] else None
+        dM = saved.pop(0) if ctx.need[1] else None
+        return (dX * g.to(dX.dtype) if dX is not None else None,
+                dM * g.to(dM.dtype) if dM is not None else None, None, None)
 
 
 class CayleyTransform(torch.nn.Module):

@@ -116,6 +116,16 @@ def test_autograd_function_gradients():
     g = oracle.loss_and_grad(X, M, 2)
     assert abs(L.item() - g["loss"]) <= 1e-10
     assert _rel(np_lib(Xd.grad), 3.0 * g["dX"]) <= 1e-8
+    # only the gradient that is asked for (M fixed), and the loss alone under no_grad
+    Xe = t_lib(X, dtype=torch.float64).requires_grad_(True)
+    Me = t_lib(M, dtype=torch.float64)
+    Le = TruncationLoss.apply(Xe, Me, plan, 2)
+    Le.backward()
+    assert abs(Le.item() - g["loss"]) <= 1e-10
+    assert _rel(np_lib(Xe.grad), g["dX"]) <= 1e-8 and Me.grad is None
+    with torch.no_grad():
+        L0 = TruncationLoss.apply(t_lib(X, dtype=torch.float64), Me, plan, 2)
+    assert abs(L0.item() - g["loss"]) <= 1e-10
     assert _rel(np_lib(Md.grad), 3.0 * g["dM"]) <= 1e-8
 
 
