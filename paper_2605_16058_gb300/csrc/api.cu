@@ -424,7 +424,20 @@ tsvdm_status second_pass(tsvdm_plan_s *p, int64_t k, const int *ranks, const int
   CK(jacobi_run<T>(jp, p->st, 0, 0, 0, 0));
   CK(jacobi_finalize_desc<T>(p->tp_desc, count, max_rho, p->st));
   T *Ktmp = (T *)p->Ahat, *Otmp = (T *)p->Wt;
-  CK(rotate_back<T>(p->tp_desc, p->tp_off, count, max_rho, kd, od, Kout, Ktmp, Otmp, S, p->st));
+  bool rotated = false;
+  if constexpr (sizeof(T) == 4) {
+    if (p->engine != JACOBI_FMA) {
+      // the gather of the other side on the CUDA cores, K R on the tensor cores
+      CK(rotate_back<T>(p->tp_desc, p->tp_off, count, max_rho, kd, od, Kout, Ktmp, Otmp, S,
+                        p->st, true));
+      CK(rotate_tc(p->tp_desc, p->tp_off, count, kd, (const float *)Kout, (float *)Ktmp,
+                   p->status, p->st));
+      *nl += 1;
+      rotated = true;
+    }
+  }
+  if (!rotated)
+    CK(rotate_back<T>(p->tp_desc, p->tp_off, count, max_rho, kd, od, Kout, Ktmp, Otmp, S, p->st));
   CK(cudaMemcpyAsync(Kout, Ktmp, sizeof(T) * kd * total, cudaMemcpyDeviceToDevice, p->st));
   CK(cudaMemcpyAsync(Oout, Otmp, sizeof(T) * od * total, cudaMemcpyDeviceToDevice, p->st));
   CK(emit_signfix<T>(p->n1, p->n2, n3, k, ranks, offsets, maxr, U, V, p->st));

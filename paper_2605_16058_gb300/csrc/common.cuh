@@ -137,11 +137,16 @@ cudaError_t complete_vectors(const T *Ahat, int64_t n1, int64_t n2, int64_t nsli
                              cudaStream_t st);
 // After the restricted Jacobi of the second pass (entries desc[0..count-1], Zr in place of
 // the other side, R, sig and perm in the entry): the other side's columns Zr(:, perm q) /
-// sig_q into Otmp, the emitted side rotated, K R(:, perm q), into Ktmp, sig_q into S.
+// sig_q into Otmp, the emitted side rotated, K R(:, perm q), into Ktmp, sig_q into S
+// (gather_only: Otmp and S alone).
 template <typename T>
 cudaError_t rotate_back(const SliceDesc *desc, const int64_t *off, int count, int max_rho,
                         int64_t kd, int64_t od, const T *Kin, T *Ktmp, T *Otmp, T *S,
-                        cudaStream_t st);
+                        cudaStream_t st, bool gather_only = false);
+// Ktmp = K R(:, perm) of rotate_back for FP32 entries on the tensor cores (three-term BF16
+// split, FP32-level accuracy).
+cudaError_t rotate_tc(const SliceDesc *desc, const int64_t *off, int count, int64_t kd,
+                      const float *Kin, float *Ktmp, int *status, cudaStream_t st);
 // Sign rule after complete_vectors on transposed slices: the largest-magnitude entry of
 // each U column positive (ties: the first), V flipped with it; a zero U column takes the
 // sign of its V column.

@@ -192,6 +192,150 @@ __global__ void __launch_bounds__(QT, 1)
   if (tid == 0 && s.fail && status) atomicOr(status, ST_TIMEOUT);
 }
 
+
+// K_i <- K_i R_i of the second pass (rotate_back): Ktmp(:, q) = K(:, 0..rho-1) R(:, perm[q])
+// for every entry of the restricted Jacobi, on the tensor cores.  A = K (kd entries x rho,
+// entries contiguous: per-element loads, one K-block value of eight per thread), B rows
+// q = R's column perm[q] (rho contiguous values); tiles of 128 entries x N <= 256 output
+// columns, the rank in K-blocks of 32; the same three-term split, stages and epilogue as
+// complete_tc_kernel.
+__global__ void __launch_bounds__(QT, 1)
+    rotate_tc_kernel(const SliceDesc *__restrict__ desc, const int64_t *__restrict__ off,
+                     int count, int64_t kd, const float *__restrict__ Kin,
+                     float *__restrict__ Ktmp, int *status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CompleteSmem &s =
+      *reinterpret_cast<CompleteSmem *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int PA[6] = {0, 0, 1, 0, 2, 1}, PB[6] = {0, 1, 0, 2, 0, 1};
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    tc::mbar_init(&s.bar[0], 1);
+    tc::mbar_init(&s.bar[1], 1);
+    tc::mbar_init_fence();
+    s.fail = 0;
+  }
+  if (warp == 0) tc::tmem_alloc_n<QN>(&s.tmem);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s.tmem;
+  uint32_t phase = 0;
+  auto wait = [&](int b) {
+    const uint32_t par = (phase >> b) & 1u;
+    if (!*(volatile int *)&s.fail && !tc::mbar_wait(&s.bar[b], par, QSPIN)) s.fail = 1;
+    phase ^= 1u << b;
+  };
+  const int64_t nct = (kd + QM - 1) / QM;
+  const int64_t ntiles = (int64_t)count * nct * 2;
+  const int ra = tid >> 2, q = tid & 3, rb = tid >> 2;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e = tile / (nct * 2);
+    const int64_t ct = (tile / 2) % nct, jt = tile % 2;
+    const SliceDesc d = desc[e];
+    const int64_t rho = d.cols;
+    const int64_t q0 = jt * QN;
+    if (q0 >= rho) continue;                      // the same decision in every thread
+    const int64_t base = off[e];
+    const int64_t ncols = rho - q0 < QN ? rho - q0 : QN;
+    const uint32_t nn = (uint32_t)((ncols + 15) / 16 * 16);
+    const int64_t c0 = ct * QM;
+    const int nkb = (int)((rho + QK - 1) / QK);
+    const uint32_t idesc = tc::instr_desc(1, QM, nn);
+    const float *R = reinterpret_cast<const float *>(d.V);
+    const bool va = c0 + ra < kd;
+    const float *acol = Kin + base * kd + c0 + ra;          // K(c0 + ra, l) at + l kd
+    const bool vb0 = rb < ncols, vb1 = rb + 128 < ncols;
+    const float *brow0 = vb0 ? R + (int64_t)d.perm[q0 + rb] * rho : R;
+    const float *brow1 = vb1 ? R + (int64_t)d.perm[q0 + rb + 128] * rho : R;
+    auto load_blk = [&](int kb, float (&xa)[8], float (&xb)[16]) {
+      const int64_t l0 = (int64_t)kb * QK + q * 8;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t l = l0 + u;
+        xa[u] = (va && l < rho) ? __ldg(acol + l * kd) : 0.f;
+        xb[u] = (vb0 && l < rho) ? __ldg(brow0 + l) : 0.f;
+        xb[8 + u] = (vb1 && l < rho) ? __ldg(brow1 + l) : 0.f;
+      }
+    };
+    auto put8 = [&](unsigned char *tiles, uint32_t term_bytes, uint32_t row, const float *x) {
+      uint32_t w[3][4];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        __nv_bfloat16 p0, p1, p2, q0_, q1, q2;
+        tc::split3(x[u], p0, p1, p2);
+        tc::split3(x[u + 1], q0_, q1, q2);
+        w[0][u / 2] = tc::pack2(p0, q0_);
+        w[1][u / 2] = tc::pack2(p1, q1);
+        w[2][u / 2] = tc::pack2(p2, q2);
+      }
+      const uint32_t offs = tc::sw64(row, (uint32_t)q);
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        *reinterpret_cast<uint4 *>(tiles + u * term_bytes + offs) =
+            make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
+    };
+    auto run_blk = [&](int kb, float (&xa)[8], float (&xb)[16], float (&na)[8],
+                       float (&nb)[16]) {
+      const int b = kb & 1;
+      if (kb >= 2) wait(b);                        // the MMAs of K-block kb-2 read stage b
+      unsigned char *st = s.st[b];
+      put8(st, QA_TERM, (uint32_t)ra, xa);
+      put8(st + 3 * QA_TERM, QB_TERM, (uint32_t)rb, xb);
+      if (nn > 128) put8(st + 3 * QA_TERM, QB_TERM, (uint32_t)(rb + 128), xb + 8);
+      if (kb + 1 < nkb) load_blk(kb + 1, na, nb);
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+          for (int m = 0; m < 6; ++m) {
+            const uint64_t da = tc::smem_desc(st + PA[m] * QA_TERM + kk * 32, 512, 4);
+            const uint64_t db = tc::smem_desc(st + 3 * QA_TERM + PB[m] * QB_TERM + kk * 32, 512, 4);
+            tc::mma_f16(tmem, da, db, idesc, (kb > 0 || kk > 0 || m > 0) ? 1u : 0u);
+          }
+        tc::mma_commit(&s.bar[b]);
+      }
+    };
+    float xa0[8], xb0[16], xa1[8], xb1[16];
+    load_blk(0, xa0, xb0);
+    for (int kb = 0; kb < nkb; kb += 2) {
+      run_blk(kb, xa0, xb0, xa1, xb1);
+      if (kb + 1 < nkb) run_blk(kb + 1, xa1, xb1, xa0, xb0);
+    }
+    for (int kb = nkb >= 2 ? nkb - 2 : 0; kb < nkb; ++kb) wait(kb & 1);
+    tc::fence_after_sync();
+    {
+      const int r = (warp & 3) * 32 + lane;
+      const int64_t c = c0 + r;
+      const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+      for (int jj = (warp >> 2) * 64; jj < (warp >> 2) * 64 + 64; jj += 16) {
+        if ((uint32_t)jj >= nn) break;
+        float dv[16];
+        tc::tmem_ld16(tmem + lane_base + (uint32_t)jj, dv);
+        if (c < kd) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int64_t qq = q0 + jj + u;
+            if (qq < rho) Ktmp[(base + qq) * kd + c] = dv[u];
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();                               // TMEM read before the next tile's MMAs
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc_n<QN>(tmem);
+  }
+  if (tid == 0 && s.fail && status) atomicOr(status, ST_TIMEOUT);
+}
+
 }  // namespace
 
 bool complete_tc_supported(const float *Ahat, const float *K, int64_t n1, int64_t n2,
@@ -216,6 +360,27 @@ cudaError_t complete_tc(const float *Ahat, int64_t n1, int64_t n2, int64_t nslic
   const int grid = (int)(ntiles < sms ? ntiles : sms);
   complete_tc_kernel<<<grid, QT, smem, st>>>(Ahat, n1, n2, nslices, k_uniform, ranks, offsets,
                                              K, S, O, status);
+  return cudaGetLastError();
+}
+
+}  // namespace tsvdm
+
+namespace tsvdm {
+
+cudaError_t rotate_tc(const SliceDesc *desc, const int64_t *off, int count, int64_t kd,
+                      const float *Kin, float *Ktmp, int *status, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = sizeof(CompleteSmem) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(rotate_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  const int64_t ntiles = (int64_t)count * ((kd + QM - 1) / QM) * 2;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  rotate_tc_kernel<<<grid, QT, smem, st>>>(desc, off, count, kd, Kin, Ktmp, status);
   return cudaGetLastError();
 }
 

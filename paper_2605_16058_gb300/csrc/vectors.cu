@@ -267,10 +267,11 @@ cudaError_t complete_vectors(const T *Ahat, int64_t n1, int64_t n2, int64_t nsli
 template <typename T>
 cudaError_t rotate_back(const SliceDesc *desc, const int64_t *off, int count, int max_rho,
                         int64_t kd, int64_t od, const T *Kin, T *Ktmp, T *Otmp, T *S,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool gather_only) {
   if (count <= 0 || max_rho <= 0) return cudaSuccess;
-  dim3 grid((unsigned)(1 + (kd + CT - 1) / CT), (unsigned)((max_rho + CT - 1) / CT),
-            (unsigned)count);
+  // gather_only: Otmp and S alone (Ktmp = K R is formed elsewhere)
+  dim3 grid((unsigned)(gather_only ? 1 : 1 + (kd + CT - 1) / CT),
+            (unsigned)((max_rho + CT - 1) / CT), (unsigned)count);
   rotate_back_kernel<T><<<grid, NT, 0, st>>>(desc, off, kd, od, Kin, Ktmp, Otmp, S);
   return cudaGetLastError();
 }
@@ -292,7 +293,7 @@ cudaError_t emit_signfix(int64_t n1, int64_t n2, int64_t nslices, int64_t k_unif
   template cudaError_t emit_signfix<T>(int64_t, int64_t, int64_t, int64_t, const int *,         \
                                        const int64_t *, int64_t, T *, T *, cudaStream_t);      \
   template cudaError_t rotate_back<T>(const SliceDesc *, const int64_t *, int, int, int64_t,    \
-                                      int64_t, const T *, T *, T *, T *, cudaStream_t);
+                                      int64_t, const T *, T *, T *, T *, cudaStream_t, bool);
 INST(float)
 INST(double)
 #undef INST
