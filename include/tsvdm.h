@@ -150,9 +150,13 @@ tsvdm_status tsvdm_plan_set_tuning(tsvdm_plan plan, int block_width, int cluster
  *                      slice); under tsvdm_plan_set_tuning, clusters caps the CTAs
  *                      launched, cluster_size and stages are ignored.
  * AUTO uses TC for F32 slices of at least 64 columns unless block_width asks for 16 or 32.
- * The engine also selects how tsvdm_reconstruct and tsvdm_backward form the slice
- * products U_i diag(S_i) V_i^T of F32 plans: tensor cores (AUTO, TC; three-term BF16
- * split, FP32-level accuracy) or FMA.
+ * The engine also selects, for F32 plans, how the other dense products are formed: the
+ * slice products U_i diag(S_i) V_i^T of tsvdm_reconstruct and tsvdm_backward and, for
+ * two-pass vectors, Z_i = A_i^T U_k and U_k R_i (tensor cores under AUTO and TC: three-term
+ * BF16 split, FP32-level accuracy; FMA otherwise), and dL/dM of tsvdm_backward and the
+ * mode-3 Gram of tsvdm_data_transform (tensor cores under AUTO and TC: two-term BF16
+ * split, three products, FP32 accumulation, FP64 sums over the split of the long mode;
+ * FMA with FP64 sums otherwise).
  * ENOTSUP for TC on an F64 plan, EINVAL for other values. */
 /* Data-driven transform (Sec. 2.2: M as the transposed matrix of left singular vectors of
  * the mode-3 unfolding A_(3), an n3 x (n1 n2) matrix; an upfront SVD of the unfolding).
