@@ -9,8 +9,12 @@
 // six products of order >= 2^-24 are accumulated, so the result has FP32-level accuracy.
 // One persistent CTA per SM (a kernel holding tensor memory runs one CTA per SM) takes
 // output tiles (slice, a-tile, b-tile); 512 threads convert (four per row of A, two per
-// row of B; the next K-block's values are loaded while the current one's MMAs run), one
-// issues the MMAs, all drain TMEM.  Stages are double-buffered; every wait is bounded.
+// row of B), one issues the MMAs, all drain TMEM.  Stages are double-buffered; every wait
+// is bounded.  Loads run one K-block ahead: a block's values are requested before the
+// previous block is converted, and a tile's first block while the previous tile's
+// accumulator drains.  Nothing consumes a loaded value before the block's barrier (S(c)
+// is loaded beside U and applied when the block is converted: a product formed at load
+// time made every thread wait for its loads at each barrier, which doubled the time).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -68,40 +72,56 @@ __global__ void __launch_bounds__(RT, 1)
   const int64_t ta = (n1 + RM - 1) / RM, tb = (n2 + RN - 1) / RN;
   const int64_t ntiles = n3 * ta * tb;
   double ss = 0.0;
+  // operand values of K-block kb: A row a0 + (tid & 127), 8 columns of chunk tid >> 7;
+  // B row b0 + (tid & 255), 16 columns of half tid >> 8
+  const int ra = tid & 127, cha = tid >> 7;
+  const int bh = tid >> 8;
+  struct TileP {
+    int64_t slice, a0, b0, c0, cnt;
+    int nkb;
+  };
+  auto tparams = [&](int64_t tile) {
+    TileP t;
+    t.slice = tile / (ta * tb);
+    t.a0 = ((tile / tb) % ta) * RM;
+    t.b0 = (tile % tb) * RN;
+    t.c0 = offsets ? offsets[t.slice] : t.slice * k;
+    t.cnt = offsets ? offsets[t.slice + 1] - t.c0 : k;
+    t.nkb = (int)((t.cnt + RK - 1) / RK);
+    return t;
+  };
+  auto load_blk = [&](const TileP &t, int kb, float (&xa)[8], float &xs, float (&xb)[16]) {
+    const int64_t arow = t.a0 + ra, bb = t.b0 + (tid & 255), c0 = t.c0, cnt = t.cnt;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int64_t c = (int64_t)kb * RK + cha * 8 + e;
+      xa[e] = (arow < n1 && c < cnt) ? __ldg(U + (c0 + c) * n1 + arow) : 0.f;
+    }
+    {
+      const int64_t c = (int64_t)kb * RK + cha * 8 + (lane & 7);
+      xs = (S && c < cnt) ? __ldg(S + c0 + c) : 1.f;
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int64_t c = (int64_t)kb * RK + bh * 16 + e;
+      // V(b, c) at (c0 + c) n2 + b, or (vtrans, uniform k) at c0 n2 + b k + c
+      xb[e] = (bb < n2 && c < cnt)
+                  ? __ldg(vtrans ? V + c0 * n2 + bb * k + c : V + (c0 + c) * n2 + bb)
+                  : 0.f;
+    }
+  };
+  float xa0[8], xs0, xb0[16], xa1[8], xs1, xb1[16];
+  TileP cur = tparams(blockIdx.x);                 // the grid never exceeds the tile count
+  if (cur.nkb > 0) load_blk(cur, 0, xa0, xs0, xb0);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t slice = tile / (ta * tb);
-    const int64_t a0 = ((tile / tb) % ta) * RM, b0 = (tile % tb) * RN;
-    const int64_t c0 = offsets ? offsets[slice] : slice * k;
-    const int64_t cnt = offsets ? offsets[slice + 1] - c0 : k;
-    const int nkb = (int)((cnt + RK - 1) / RK);
-    // operand values of K-block kb: A row a0 + (tid & 127), 8 columns of chunk tid >> 7;
-    // B row b0 + (tid & 255), 16 columns of half tid >> 8
-    const int ra = tid & 127, cha = tid >> 7;
-    const int64_t arow = a0 + ra;
-    const int64_t bb = b0 + (tid & 255);
-    const int bh = tid >> 8;
-    auto load_blk = [&](int kb, float (&xa)[8], float (&xb)[16]) {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int64_t c = (int64_t)kb * RK + cha * 8 + e;
-        xa[e] = (arow < n1 && c < cnt)
-                    ? __ldg(U + (c0 + c) * n1 + arow) * (S ? __ldg(S + c0 + c) : 1.f)
-                    : 0.f;
-      }
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int64_t c = (int64_t)kb * RK + bh * 16 + e;
-        // V(b, c) at (c0 + c) n2 + b, or (vtrans, uniform k) at c0 n2 + b k + c
-        xb[e] = (bb < n2 && c < cnt)
-                    ? __ldg(vtrans ? V + c0 * n2 + bb * k + c : V + (c0 + c) * n2 + bb)
-                    : 0.f;
-      }
-    };
+    const int64_t slice = cur.slice, a0 = cur.a0, b0 = cur.b0;
+    const int nkb = cur.nkb;
     // one K-block: the operands already in registers go to stage kb & 1 as three BF16
     // terms, the next block's values are loaded while this one's MMAs run
-    auto run_blk = [&](int kb, float (&xa)[8], float (&xb)[16], float (&na)[8],
-                       float (&nb)[16]) {
+    auto run_blk = [&](int kb, float (&xa)[8], float &xs, float (&xb)[16],
+                       float (&na)[8], float &ns, float (&nb)[16]) {
       const int b = kb & 1;
+      if (kb + 1 < nkb) load_blk(cur, kb + 1, na, ns, nb);
       if (kb >= 2) wait(b);                        // the MMAs of K-block kb-2 read stage b
       unsigned char *st = s.st[b];
       {
@@ -109,8 +129,8 @@ __global__ void __launch_bounds__(RT, 1)
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
           __nv_bfloat16 p0, p1, p2, q0, q1, q2;
-          tc::split3(xa[e], p0, p1, p2);
-          tc::split3(xa[e + 1], q0, q1, q2);
+          tc::split3(xa[e] * __shfl_sync(0xffffffffu, xs, e), p0, p1, p2);
+          tc::split3(xa[e + 1] * __shfl_sync(0xffffffffu, xs, e + 1), q0, q1, q2);
           w[0][e / 2] = tc::pack2(p0, q0);
           w[1][e / 2] = tc::pack2(p1, q1);
           w[2][e / 2] = tc::pack2(p2, q2);
@@ -140,7 +160,6 @@ __global__ void __launch_bounds__(RT, 1)
           *reinterpret_cast<uint4 *>(st + 3 * A_TERM + u * B_TERM + off) =
               make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
       }
-      if (kb + 1 < nkb) load_blk(kb + 1, na, nb);
       tc::fence_proxy_async();
       tc::fence_before_sync();
       __syncthreads();
@@ -157,11 +176,16 @@ __global__ void __launch_bounds__(RT, 1)
         tc::mma_commit(&s.bar[b]);
       }
     };
-    float xa0[8], xb0[16], xa1[8], xb1[16];
-    if (nkb > 0) load_blk(0, xa0, xb0);
     for (int kb = 0; kb < nkb; kb += 2) {
-      run_blk(kb, xa0, xb0, xa1, xb1);
-      if (kb + 1 < nkb) run_blk(kb + 1, xa1, xb1, xa0, xb0);
+      run_blk(kb, xa0, xs0, xb0, xa1, xs1, xb1);
+      if (kb + 1 < nkb) run_blk(kb + 1, xa1, xs1, xb1, xa0, xs0, xb0);
+    }
+    // the next tile's first K-block is loaded while this tile's MMAs finish and its
+    // accumulator drains (both register sets are free here)
+    TileP nxt = cur;
+    if (tile + gridDim.x < ntiles) {
+      nxt = tparams(tile + gridDim.x);
+      if (nxt.nkb > 0) load_blk(nxt, 0, xa0, xs0, xb0);
     }
     for (int kb = nkb >= 2 ? nkb - 2 : 0; kb < nkb; ++kb) wait(kb & 1);
     tc::fence_after_sync();
@@ -194,6 +218,7 @@ __global__ void __launch_bounds__(RT, 1)
     }
     tc::fence_before_sync();
     __syncthreads();                               // TMEM read before the next tile's MMAs
+    cur = nxt;
   }
   if constexpr (SS) {
 #pragma unroll
